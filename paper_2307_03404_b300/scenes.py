@@ -1,0 +1,441 @@
+"""Seeded synthetic inputs: sparse voxel grids, cameras and RGB-D sensor frames.
+
+This module is shared by the CUDA path's tests and benchmark and by the CPU
+oracle's tests. It holds none of the rendering method's arithmetic (no
+compositing, no SH, no interpolation, no pose algebra beyond building camera
+frames): it only builds the grid arrays of an analytic scene, places cameras,
+and simulates an RGB-D sensor by intersecting pixel rays with the analytic
+primitives. The paper measures on Replica and ScanNet, which are not
+available; these scenes stand in for them at the paper's camera model
+(640x480, f = 525) and its grid form (28 values per allocated vertex, a dense
+int32 link array, Sec. 5.2, Sec. 6.1).
+
+Everything is drawn from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Sequence
+
+import numpy as np
+
+N_VALUES = 28          # 1 density + 3 x 9 SH coefficients per vertex (Sec. 5.2)
+N_SH = 27
+
+
+@dataclasses.dataclass
+class Grid:
+    """Sparse voxel grid in the canonical caller layout.
+
+    ``links[z, y, x]`` is the row of vertex (x, y, z) in ``density`` / ``sh``,
+    or -1 where the vertex is not allocated. ``sh[i]`` is channel-major
+    (R0..R8, G0..G8, B0..B8). Vertex (x, y, z) sits at lo + (x, y, z) * h with
+    h = (hi - lo) / (res - 1).
+    """
+
+    res: tuple
+    lo: np.ndarray
+    hi: np.ndarray
+    links: np.ndarray      # int32 [Rz, Ry, Rx]
+    density: np.ndarray    # float32 [n]
+    sh: np.ndarray         # float32 [n, 27]
+
+    @property
+    def n_alloc(self) -> int:
+        return int(self.density.shape[0])
+
+    @property
+    def h(self) -> np.ndarray:
+        return (np.asarray(self.hi, np.float64) - np.asarray(self.lo, np.float64)) / (
+            np.asarray(self.res, np.float64) - 1.0)
+
+    def with_values(self, density, sh) -> "Grid":
+        return Grid(self.res, self.lo, self.hi, self.links, density, sh)
+
+
+@dataclasses.dataclass
+class Camera:
+    """Pinhole camera: intrinsics in pixels, camera-to-world pose [R | o]
+    (x right, y down, z forward in the camera frame)."""
+
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+    T_wc: np.ndarray       # float64 [3, 4]
+
+    def with_pose(self, T_wc) -> "Camera":
+        return Camera(self.fx, self.fy, self.cx, self.cy, self.width, self.height,
+                      np.asarray(T_wc, np.float64).reshape(3, 4).copy())
+
+
+@dataclasses.dataclass
+class Scene:
+    """A grid with the analytic primitives it was built from."""
+
+    grid: Grid
+    prims: list
+    room_lo: np.ndarray | None = None
+    room_hi: np.ndarray | None = None
+
+
+# ------------------------------------------------------------------ cameras
+def look_at(eye, target, up=(0.0, 1.0, 0.0)) -> np.ndarray:
+    """Camera-to-world [R | eye] for a camera at ``eye`` looking at ``target``."""
+    eye = np.asarray(eye, np.float64)
+    z = np.asarray(target, np.float64) - eye
+    z /= np.linalg.norm(z)
+    x = np.cross(z, np.asarray(up, np.float64))
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    T = np.zeros((3, 4))
+    T[:, 0], T[:, 1], T[:, 2], T[:, 3] = x, y, z, eye
+    return T
+
+
+def perturb_pose(T_wc, trans_m: float, rot_deg: float, rng) -> np.ndarray:
+    """Move a pose by ``trans_m`` along a random unit axis and rotate it by
+    ``rot_deg`` about a random axis (world frame, left)."""
+    from scipy.spatial.transform import Rotation
+
+    T = np.asarray(T_wc, np.float64).reshape(3, 4)
+    u = rng.standard_normal(3)
+    u /= np.linalg.norm(u)
+    a = rng.standard_normal(3)
+    a /= np.linalg.norm(a)
+    Rp = Rotation.from_rotvec(np.deg2rad(rot_deg) * a).as_matrix()
+    out = np.zeros((3, 4))
+    out[:, :3] = Rp @ T[:, :3]
+    out[:, 3] = Rp @ T[:, 3] + trans_m * u
+    return out
+
+
+def dense_rays(cams: Sequence[Camera]):
+    """(cam_id, pixel) of every pixel of every camera, camera by camera."""
+    cid, pix = [], []
+    for i, c in enumerate(cams):
+        n = int(c.width) * int(c.height)
+        cid.append(np.full(n, i, np.int32))
+        pix.append(np.arange(n, dtype=np.int32))
+    return np.concatenate(cid), np.concatenate(pix)
+
+
+def random_rays(cams: Sequence[Camera], n: int, seed: int):
+    """``n`` distinct rays drawn uniformly from all pixels of all cameras."""
+    cid, pix = dense_rays(cams)
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(cid.shape[0], size=min(n, cid.shape[0]), replace=False))
+    return cid[sel], pix[sel]
+
+
+# ------------------------------------------------------------ tiny grids
+def tiny_grid(R: int = 6, seed: int = 0, alloc_frac: float = 1.0, half: float = 1.0,
+              sigma_mean: float = 3.0, sigma_std: float = 1.0, sh_std: float = 0.3,
+              border: int = 0) -> Grid:
+    """Small random grid for finite differences and closed forms.
+
+    ``alloc_frac`` < 1 leaves a random subset of vertices unallocated;
+    ``border`` layers of vertices at the box faces are left unallocated.
+    """
+    rng = np.random.default_rng(seed)
+    alloc = rng.random((R, R, R)) < alloc_frac
+    if border > 0:
+        b = border
+        inner = np.zeros((R, R, R), bool)
+        inner[b:R - b, b:R - b, b:R - b] = True
+        alloc &= inner
+    links = np.full((R, R, R), -1, np.int32)
+    n = int(alloc.sum())
+    order = rng.permutation(n).astype(np.int32)
+    links[alloc] = order
+    density = (sigma_mean + sigma_std * rng.standard_normal(n)).astype(np.float32)
+    sh = (sh_std * rng.standard_normal((n, N_SH))).astype(np.float32)
+    lo = np.full(3, -half)
+    hi = np.full(3, half)
+    return Grid((R, R, R), lo, hi, links, density, sh)
+
+
+def constant_grid(R: int, sigma: float, sh_dc: Sequence[float], half: float = 1.0) -> Grid:
+    """Every vertex allocated with the same density and only the degree-0 SH
+    coefficient set (``sh_dc`` per channel)."""
+    n = R ** 3
+    links = np.arange(n, dtype=np.int32).reshape(R, R, R)
+    density = np.full(n, sigma, np.float32)
+    sh = np.zeros((n, N_SH), np.float32)
+    for ch in range(3):
+        sh[:, 9 * ch] = sh_dc[ch]
+    return Grid((R, R, R), np.full(3, -half), np.full(3, half), links, density, sh)
+
+
+# ------------------------------------------------- dense 64^3 sphere scene
+def sphere_scene(R: int = 64, seed: int = 1001, width: int = 64, height: int = 48,
+                 f: float = 60.0):
+    """Dense R^3 grid over [-1,1]^3: density 40 inside three random spheres
+    (centres in [-0.5,0.5]^3, radius 0.15-0.35) and in the floor slab
+    y <= -0.8, 0 elsewhere; the two outermost vertex layers are 0; SH ~ N(0,0.3).
+    One camera on the radius-2.5 sphere (elevation 10-60 deg) looking at the
+    origin. Also returns a perturbed copy of the grid (density * (1 + 0.1 N),
+    SH + N(0, 0.05)) from which targets are rendered.
+    """
+    rng = np.random.default_rng(seed)
+    xs = np.linspace(-1.0, 1.0, R)
+    Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+    occ = Y <= -0.8
+    for _ in range(3):
+        c = rng.uniform(-0.5, 0.5, 3)
+        r = rng.uniform(0.15, 0.35)
+        occ |= (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2 <= r * r
+    dens = np.where(occ, 40.0, 0.0)
+    dens[:2], dens[-2:] = 0.0, 0.0
+    dens[:, :2], dens[:, -2:] = 0.0, 0.0
+    dens[:, :, :2], dens[:, :, -2:] = 0.0, 0.0
+    n = R ** 3
+    links = np.arange(n, dtype=np.int32).reshape(R, R, R)
+    density = dens.reshape(-1).astype(np.float32)
+    sh = (0.3 * rng.standard_normal((n, N_SH))).astype(np.float32)
+    grid = Grid((R, R, R), np.full(3, -1.0), np.full(3, 1.0), links, density, sh)
+    az = rng.uniform(0, 2 * np.pi)
+    el = np.deg2rad(rng.uniform(10, 60))
+    eye = 2.5 * np.array([np.cos(el) * np.cos(az), np.sin(el), np.cos(el) * np.sin(az)])
+    cam = Camera(f, f, width / 2.0, height / 2.0, width, height, look_at(eye, (0, 0, 0)))
+    pd = (density * (1.0 + 0.1 * rng.standard_normal(n))).astype(np.float32)
+    ps = (sh + 0.05 * rng.standard_normal((n, N_SH))).astype(np.float32)
+    return grid, cam, grid.with_values(pd, ps)
+
+
+# ------------------------------------------------------------- room scenes
+def _box_sdf(P, c, half):
+    q = np.abs(P - c) - half
+    outside = np.linalg.norm(np.maximum(q, 0.0), axis=-1)
+    inside = np.minimum(q.max(axis=-1), 0.0)
+    return outside + inside
+
+
+def _prim_sdf(P, prim):
+    if prim["kind"] == "sphere":
+        return np.linalg.norm(P - prim["c"], axis=-1) - prim["r"]
+    return _box_sdf(P, prim["c"], prim["half"])
+
+
+def _prim_bounds(prim):
+    ext = prim["r"] if prim["kind"] == "sphere" else np.max(prim["half"])
+    return prim["c"] - ext * np.sqrt(3.0), prim["c"] + ext * np.sqrt(3.0)
+
+
+def _random_prims(rng, room_lo, room_hi, n):
+    prims = []
+    span = room_hi - room_lo
+    for i in range(n):
+        rgb = rng.uniform(0.1, 0.9, 3)
+        if i % 2 == 0:
+            r = rng.uniform(0.04, 0.12) * span.min()
+            c = rng.uniform(room_lo + r, room_hi - r)
+            prims.append({"kind": "sphere", "c": c, "r": r, "rgb": rgb})
+        else:
+            half = rng.uniform(0.03, 0.12, 3) * span.min()
+            c = rng.uniform(room_lo + half, room_hi - half)
+            c[1] = room_lo[1] + half[1] if rng.random() < 0.5 else c[1]  # some on the floor
+            prims.append({"kind": "box", "c": c, "half": half, "rgb": rgb})
+    return prims
+
+
+def _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims, dtype=np.float32):
+    """Signed distance (positive in free space) at every vertex, built slab by
+    slab over z; walls are the faces of the room box, solid outside it."""
+    xs = np.linspace(lo[0], hi[0], R).astype(dtype)
+    ys = np.linspace(lo[1], hi[1], R).astype(dtype)
+    zs = np.linspace(lo[2], hi[2], R).astype(dtype)
+    wx = np.minimum(xs - room_lo[0], room_hi[0] - xs).astype(dtype)
+    wy = np.minimum(ys - room_lo[1], room_hi[1] - ys).astype(dtype)
+    wz = np.minimum(zs - room_lo[2], room_hi[2] - zs).astype(dtype)
+    s = np.empty((R, R, R), dtype)
+    np.minimum(wz[:, None, None], wy[None, :, None], out=s)
+    np.minimum(s, wx[None, None, :], out=s)
+    h = (hi - lo) / (R - 1)
+    for p in prims:
+        blo, bhi = _prim_bounds(p)
+        i0 = np.clip(np.floor((blo - lo) / h).astype(int) - 3, 0, R - 1)
+        i1 = np.clip(np.ceil((bhi - lo) / h).astype(int) + 4, 0, R)
+        sub = s[i0[2]:i1[2], i0[1]:i1[1], i0[0]:i1[0]]
+        Zs, Ys, Xs = np.meshgrid(zs[i0[2]:i1[2]], ys[i0[1]:i1[1]], xs[i0[0]:i1[0]],
+                                 indexing="ij")
+        P = np.stack([Xs, Ys, Zs], axis=-1).astype(np.float64)
+        np.minimum(sub, _prim_sdf(P, p).astype(dtype), out=sub)
+    return s
+
+
+def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 3.2,
+               wall_inset_vox: float = 4.0, border: int = 2) -> Scene:
+    """Analytic room: the six faces of a box inset by ``wall_inset_vox`` voxels
+    from the grid box, plus ``n_prims`` random spheres and boxes. Vertices
+    within a band around the surfaces are allocated; the band width is the
+    quantile of |sdf| that allocates the fraction ``occupancy`` of all
+    vertices. The ``border`` outermost vertex layers are never allocated.
+    Allocated density rises across the band into the solid, about 0.6 / h at
+    the inner band edge and slightly negative at the outer one; SH ~ N(0, 0.3).
+    """
+    rng = np.random.default_rng(seed)
+    lo = np.full(3, -half)
+    hi = np.full(3, half)
+    h = (hi - lo) / (R - 1)
+    room_lo = lo + wall_inset_vox * h
+    room_hi = hi - wall_inset_vox * h
+    prims = _random_prims(rng, room_lo, room_hi, n_prims)
+    s = _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims)
+    b = border
+    inner = np.zeros(R, bool)
+    inner[b:R - b] = True
+    st = max(1, R // 128)
+    sample = np.abs(s[::st, ::st, ::st]).reshape(-1)
+    w = float(np.quantile(sample, occupancy))
+    alloc = np.abs(s) <= w
+    alloc &= inner[:, None, None] & inner[None, :, None] & inner[None, None, :]
+    n = int(alloc.sum())
+    links = np.full((R, R, R), -1, np.int32)
+    links[alloc] = np.arange(n, dtype=np.int32)
+    sv = s[alloc].astype(np.float64)
+    hm = float(h.min())
+    density = ((0.6 / hm) * (0.5 - 0.6 * sv / w)
+               + (0.05 / hm) * rng.standard_normal(n)).astype(np.float32)
+    sh = rng.standard_normal((n, N_SH), dtype=np.float32)
+    sh *= np.float32(0.3)
+    del s
+    grid = Grid((R, R, R), lo, hi, links, density, sh)
+    return Scene(grid, prims, room_lo, room_hi)
+
+
+def _free_space(scene: Scene, P):
+    P = np.atleast_2d(P)
+    d = np.minimum((P - scene.room_lo).min(axis=-1), (scene.room_hi - P).min(axis=-1))
+    for p in scene.prims:
+        d = np.minimum(d, _prim_sdf(P, p))
+    return d
+
+
+def room_cameras(scene: Scene, n: int, seed: int, width: int = 640, height: int = 480,
+                 f: float = 525.0, clearance: float = 0.5) -> List[Camera]:
+    """``n`` keyframes on a Catmull-Rom spline through six random free-space
+    points of the room, each looking along the path with a small random yaw
+    and a slight downward pitch."""
+    rng = np.random.default_rng(seed)
+    span = scene.room_hi - scene.room_lo
+    pts = []
+    while len(pts) < 6:
+        p = rng.uniform(scene.room_lo + 0.2 * span, scene.room_hi - 0.2 * span)
+        if _free_space(scene, p)[0] > clearance:
+            pts.append(p)
+    pts = np.array(pts)
+    ctrl = np.vstack([pts[:1], pts, pts[-1:]])
+
+    def spline(u):
+        seg = min(int(u), len(pts) - 2)
+        t = u - seg
+        p0, p1, p2, p3 = ctrl[seg], ctrl[seg + 1], ctrl[seg + 2], ctrl[seg + 3]
+        pos = 0.5 * ((2 * p1) + (-p0 + p2) * t + (2 * p0 - 5 * p1 + 4 * p2 - p3) * t * t
+                     + (-p0 + 3 * p1 - 3 * p2 + p3) * t ** 3)
+        tan = 0.5 * ((-p0 + p2) + 2 * (2 * p0 - 5 * p1 + 4 * p2 - p3) * t
+                     + 3 * (-p0 + 3 * p1 - 3 * p2 + p3) * t * t)
+        return pos, tan
+
+    cams = []
+    for i in range(n):
+        u = (len(pts) - 1) * (i + 0.5) / n
+        pos, tan = spline(u)
+        fwd = np.array([tan[0], 0.0, tan[2]])
+        if np.linalg.norm(fwd) < 1e-6:
+            fwd = np.array([1.0, 0.0, 0.0])
+        fwd /= np.linalg.norm(fwd)
+        yaw = np.deg2rad(rng.uniform(-10, 10))
+        pitch = np.deg2rad(rng.uniform(-15, 0))
+        cy_, sy_ = np.cos(yaw), np.sin(yaw)
+        fwd = np.array([cy_ * fwd[0] - sy_ * fwd[2], 0.0, sy_ * fwd[0] + cy_ * fwd[2]])
+        look = np.cos(pitch) * fwd + np.array([0.0, np.sin(pitch), 0.0])
+        cams.append(Camera(f, f, width / 2.0 - 0.5, height / 2.0 - 0.5, width, height,
+                           look_at(pos, pos + look)))
+    return cams
+
+
+def sensor_frames(scene: Scene, cams: Sequence[Camera], seed: int, depth_noise: float = 0.01,
+                  missing: float = 0.02):
+    """Simulated RGB-D frames: per pixel, the first analytic surface hit along
+    the pinhole ray gives the z-depth (noise N(0, (depth_noise z^2)^2), a
+    fraction ``missing`` of pixels set to 0 = invalid) and a colour (the
+    primitive's base colour with a smooth pattern, clipped to [0, 1]).
+    Returns (rgb [n,3] float32, depth_z [n] float32) for ``dense_rays(cams)``.
+    """
+    rng = np.random.default_rng(seed)
+    rgbs, depths = [], []
+    wall_rgb = np.array([[0.8, 0.75, 0.7], [0.6, 0.65, 0.7], [0.5, 0.5, 0.45]])
+    for cam in cams:
+        W, H = int(cam.width), int(cam.height)
+        u, v = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+        dc = np.stack([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, np.ones_like(u)], -1)
+        dc = dc.reshape(-1, 3)
+        zlen = np.linalg.norm(dc, axis=-1)
+        T = np.asarray(cam.T_wc, np.float64).reshape(3, 4)
+        d = (dc @ T[:, :3].T) / zlen[:, None]
+        o = T[:, 3]
+        # walls: exit of the room box
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ta = (scene.room_lo - o) / d
+            tb = (scene.room_hi - o) / d
+        tfar = np.maximum(ta, tb)
+        tfar = np.where(np.isfinite(tfar), tfar, np.inf)
+        axis = np.argmin(tfar, axis=-1)
+        t_best = np.min(tfar, axis=-1)
+        col = wall_rgb[axis]
+        for p in scene.prims:
+            if p["kind"] == "sphere":
+                oc = o - p["c"]
+                bq = d @ oc
+                cq = oc @ oc - p["r"] ** 2
+                disc = bq * bq - cq
+                th = -bq - np.sqrt(np.maximum(disc, 0.0))
+                hit = (disc > 0) & (th > 1e-6)
+            else:
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    t1 = (p["c"] - p["half"] - o) / d
+                    t2 = (p["c"] + p["half"] - o) / d
+                tn = np.nanmax(np.minimum(t1, t2), axis=-1)
+                tf = np.nanmin(np.maximum(t1, t2), axis=-1)
+                th = tn
+                hit = (tf > tn) & (tn > 1e-6)
+            closer = hit & (th < t_best)
+            t_best = np.where(closer, th, t_best)
+            col = np.where(closer[:, None], p["rgb"][None, :], col)
+        X = o + t_best[:, None] * d
+        pattern = 0.5 + 0.5 * np.sin(7.0 * X[:, 0]) * np.cos(5.0 * X[:, 2] + 3.0 * X[:, 1])
+        rgb = np.clip(col * (0.7 + 0.3 * pattern[:, None])
+                      + 0.01 * rng.standard_normal((W * H, 3)), 0.0, 1.0)
+        z = t_best / zlen
+        z = z + depth_noise * z * z * rng.standard_normal(W * H)
+        z[rng.random(W * H) < missing] = 0.0
+        rgbs.append(rgb.astype(np.float32))
+        depths.append(z.astype(np.float32))
+    return np.concatenate(rgbs), np.concatenate(depths)
+
+
+def mixed_resolution_cameras(scene: Scene, n: int, seed: int,
+                             sizes=((320, 240), (640, 480), (848, 480), (1200, 680))):
+    """``n`` keyframes whose resolution is drawn uniformly from ``sizes``,
+    focal length scaled with the width (525 px at 640)."""
+    rng = np.random.default_rng(seed)
+    base = room_cameras(scene, n, seed + 7)
+    out = []
+    for c in base:
+        W, H = sizes[int(rng.integers(len(sizes)))]
+        f = 525.0 * W / 640.0
+        out.append(Camera(f, f, W / 2.0 - 0.5, H / 2.0 - 0.5, W, H, c.T_wc))
+    return out
+
+
+# ----------------------------------------------------- named workloads
+WORKLOADS = {
+    # name: (R, occupancy, n_prims, seed)
+    "room256": (256, 0.10, 20, 1002),
+    "room512": (512, 0.05, 20, 1003),
+    "room512mix": (512, 0.05, 20, 1004),
+    "room1024": (1024, 0.02, 200, 1005),
+}
