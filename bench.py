@@ -1,0 +1,470 @@
+"""Benchmark: mapping rays/s (forward + backward to the grid) and tracking
+iterations/s at 640x480, on seeded synthetic scenes.
+
+Workload (one step): every ray of 8 keyframes of 640x480 (2,457,600 rays)
+through a 256^3 grid with 10% of vertices allocated (analytic room with 20
+primitives): forward render (Eq. 1-3), RGB-D loss (Eq. 4, 5, 11) and its
+gradient to every grid value (Eq. 6-10), written into a zeroed gradient
+buffer. Tracking: 100 Gauss-Newton iterations (pose Jacobian + FP64 solve +
+SE(3) step) on one 640x480 frame against a 512^3 grid with 5% allocated,
+captured in one CUDA graph.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank maps its own 8 keyframes of the same scene (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mapping rays/s fwd+bwd & tracking iters/s @640x480, % HBM roofline, vs FP32"
+FRAMES_PER_RANK = 8
+FALLBACK_HBM_GBS = 6400.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def shard_frames(world: int, rank: int, per_rank: int = FRAMES_PER_RANK):
+    """Keyframe indices of ``rank`` when ``world`` ranks each map ``per_rank``
+    keyframes of one trajectory of ``world * per_rank`` keyframes."""
+    return list(range(rank * per_rank, (rank + 1) * per_rank))
+
+
+def combine_rank_times(times_ms, units_per_rank):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    t = max(times_ms)
+    return sum(units_per_rank) / (t / 1e3), t
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.dev = device_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+def mapping_workload(world, rank):
+    from paper_2307_03404_b300 import scenes
+
+    R, occ, npr, seed = scenes.WORKLOADS["room256"]
+    t = time.time()
+    sc = scenes.room_scene(R, occ, npr, seed)
+    cams_all = scenes.room_cameras(sc, FRAMES_PER_RANK * world, seed + 1)
+    cams = [cams_all[i] for i in shard_frames(world, rank)]
+    rgb_t, depth_t = scenes.sensor_frames(sc, cams, seed + 2 + rank)
+    opts = dict(step=0.5 * float(sc.grid.h[0]), lambda_d=1.0, depth_is_z=True)
+    log(f"[bench] room256 scene + frames in {time.time() - t:.1f}s, n_alloc {sc.grid.n_alloc}")
+    return sc, cams, rgb_t, depth_t, opts
+
+
+def workload_config(sc, cams, storage):
+    n = sum(c.width * c.height for c in cams)
+    return {"workload": f"room256: 256^3 grid, {sc.grid.n_alloc} of {256 ** 3} vertices "
+                        f"allocated (10%), {len(cams)} keyframes 640x480 = {n} rays; "
+                        "forward + RGB-D loss + backward to the grid",
+            "storage": storage, "step_voxels": 0.5, "lambda_d": 1.0,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2307_03404_b300 import plx, scenes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sc, cams_np, rgb_np, depth_np, opts = mapping_workload(world, rank)
+    n_rays = rgb_np.shape[0]
+    cams = plx.CameraSet(cams_np)
+    o = plx.opts_from_dict(opts)
+    rgb_t = torch.from_numpy(rgb_np).cuda()
+    depth_t = torch.from_numpy(depth_np).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def measure(storage, K, W, with_e2e):
+        grid = plx.Grid.from_scene(sc.grid, storage)
+        fw = {"rgb": torch.empty(n_rays, 3, device="cuda"),
+              "depth": torch.empty(n_rays, device="cuda"),
+              "state": torch.empty(n_rays, device="cuda"), "counts": None}
+        grad = torch.zeros(grid.n_alloc, plx.GRAD_STRIDE, device="cuda")
+        loss = torch.empty(2, device="cuda", dtype=torch.float64)
+
+        def step(ev=None):
+            grad.zero_()
+            if ev:
+                ev[0].record()
+            plx.render_forward(grid, cams, o, out=fw)
+            if ev:
+                ev[1].record()
+            plx.render_backward_grid(grid, cams, o, rgb_t, depth_t, fw["rgb"], fw["depth"],
+                                     grad=grad, loss=loss)
+            if ev:
+                ev[2].record()
+
+        for _ in range(W):
+            step()
+        barrier()
+        E = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+        for e in E:
+            flush.fill_(1)
+            e[3].record()
+            step(e)
+            e[4].record()
+        barrier()
+        step_ms = [e[3].elapsed_time(e[4]) for e in E]
+        fwd_ms = [e[0].elapsed_time(e[1]) for e in E]
+        bwd_ms = [e[1].elapsed_time(e[2]) for e in E]
+        res = {"step_ms": step_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+               "loss": loss.cpu().tolist()}
+        if with_e2e:
+            rgb_h = torch.from_numpy(rgb_np).pin_memory()
+            depth_h = torch.from_numpy(depth_np).pin_memory()
+            poses_h = cams.poses.cpu().pin_memory()
+            loss_h = torch.empty(2, dtype=torch.float64).pin_memory()
+            rgb_d, depth_d = torch.empty_like(rgb_t), torch.empty_like(depth_t)
+
+            def e2e_step():
+                rgb_d.copy_(rgb_h, non_blocking=True)
+                depth_d.copy_(depth_h, non_blocking=True)
+                cams.poses.copy_(poses_h, non_blocking=True)
+                grad.zero_()
+                plx.render_forward(grid, cams, o, out=fw)
+                plx.render_backward_grid(grid, cams, o, rgb_d, depth_d, fw["rgb"], fw["depth"],
+                                         grad=grad, loss=loss)
+                loss_h.copy_(loss, non_blocking=True)
+
+            for _ in range(W):
+                e2e_step()
+            barrier()
+            E2 = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+            for e in E2:
+                flush.fill_(1)
+                e[0].record()
+                e2e_step()
+                e[1].record()
+            barrier()
+            res["e2e_ms"] = [e[0].elapsed_time(e[1]) for e in E2]
+            res["h2d"] = rgb_h.numel() * 4 + depth_h.numel() * 4 + poses_h.numel() * 8
+            res["d2h"] = loss_h.numel() * 8
+        # exact sample counts for the byte model (untimed)
+        cnt = plx.render_forward(grid, cams, o, counts=True)["counts"].cpu().numpy()
+        res["counts"] = cnt
+        grid.close()
+        return res
+
+    K, W = args.steps, args.warmup
+    dev_id = torch.cuda.current_device()
+    try:
+        smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev_id).uuid)
+    except Exception:
+        smi_id = str(dev_id)
+    with ClockSampler(smi_id) as clk:
+        main = measure(args.storage, K, W, with_e2e=True)
+        other_storage = "bf16" if args.storage == "f32" else "f32"
+        other = measure(other_storage, K, W, with_e2e=False)
+    clocks = clk.summary()
+
+    # whole-job numbers: max over ranks
+    def rank_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t_main = rank_max(sum(main["step_ms"]))
+    t_e2e = rank_max(sum(main["e2e_ms"]))
+    t_other = rank_max(sum(other["step_ms"]))
+    rays_job = n_rays * world * K
+    value = rays_job / (t_main / 1e3)
+
+    # byte model of the dominant kernel (grid backward) and of the step
+    valid = np.isfinite(depth_np) & (depth_np > 0)
+    hbm, peak_kind = peaks()
+
+    def bytes_model(counts, storage):
+        rec = 896.0 if storage == "f32" else 448.0
+        s_all = counts[:, 0].astype(np.float64)
+        s_occ = counts[:, 1].astype(np.float64)
+        fwd = (s_all * 32 + s_occ * rec).sum() + 20.0 * n_rays
+        bwd = (s_all[valid] * 32 + s_occ[valid] * (rec + 1792.0)).sum() + 32.0 * valid.sum() \
+            + 4.0 * n_rays
+        return fwd, bwd, float(s_all.mean()), float(s_occ.mean())
+
+    fwd_b, bwd_b, s_all, s_occ = bytes_model(main["counts"], args.storage)
+    fwd_ms, bwd_ms = statistics.mean(main["fwd_ms"]), statistics.mean(main["bwd_ms"])
+    dom = "backward_grid" if bwd_ms >= fwd_ms else "forward"
+    dom_b, dom_ms = (bwd_b, bwd_ms) if dom == "backward_grid" else (fwd_b, fwd_ms)
+    achieved = dom_b / (dom_ms / 1e3) / 1e9
+    step_roof = (fwd_b + bwd_b) / (hbm * 1e9) * 1e3   # ms per step at the HBM roof
+    fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": t_main / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(sc, cams_np, args.storage),
+                       parallelism=f"replicated grid, keyframes sharded over {world} rank(s)"),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "bytes_per_launch": dom_b, "ms_per_launch": dom_ms,
+                     "step_frac": step_roof / (t_main / K),
+                     "S_all_mean": s_all, "S_occ_mean": s_occ},
+        "e2e": {"value": rays_job / (t_e2e / 1e3), "unit": "rays/s",
+                "h2d_bytes_per_step": main["h2d"], "d2h_bytes_per_step": main["d2h"]},
+        "gpu_launches": K * 3,
+        "clocks": clocks,
+        other_storage: {"value": rays_job / (t_other / 1e3), "unit": "rays/s",
+                        "ms_per_step": t_other / K,
+                        "step_frac": (fo_b + bo_b) / (hbm * 1e9) * 1e3 / (t_other / K)},
+        "loss": main["loss"],
+    }
+    if not args.no_tracking:
+        line["tracking"] = run_tracking(args, world, rank, barrier)
+    if not args.no_cpu and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(sc, cams_np, rgb_np, depth_np, opts, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_tracking(args, world, rank, barrier):
+    """Tracking iterations/s: 100 GN iterations in one CUDA graph."""
+    import torch
+
+    from paper_2307_03404_b300 import plx, scenes
+
+    R, occ, npr, seed = scenes.WORKLOADS[args.tracking_workload]
+    t = time.time()
+    sc = scenes.room_scene(R, occ, npr, seed)
+    cam = scenes.room_cameras(sc, 1, seed + 1 + rank)[0]
+    log(f"[bench] {args.tracking_workload} tracking scene in {time.time() - t:.1f}s")
+    opts = dict(step=0.5 * float(sc.grid.h[0]), lambda_d=1.0, depth_is_z=False)
+    o = plx.opts_from_dict(opts)
+    T0 = scenes.perturb_pose(cam.T_wc, 0.03, 2.0, np.random.default_rng(seed + 5))
+    iters = args.tracking_iters
+    out = {"workload": f"{args.tracking_workload}: {R}^3 grid, {sc.grid.n_alloc} allocated, "
+                       f"one 640x480 frame, {iters} GN iterations per CUDA graph, "
+                       "targets rendered at the true pose, start perturbed 3 cm / 2 deg",
+           "unit": "iters/s"}
+    for storage in ("f32", "bf16"):
+        grid = plx.Grid.from_scene(sc.grid, storage)
+        cams = plx.CameraSet([cam])
+        tg = plx.render_forward(grid, cams, o)       # targets at the true pose
+        rgb_t, depth_t = tg["rgb"].clone(), tg["depth"].clone()
+        cams.poses.copy_(torch.tensor(T0.reshape(1, 12), device="cuda"))
+        start = cams.poses.clone()
+        H = torch.empty(6, 6, device="cuda", dtype=torch.float64)
+        b = torch.empty(6, device="cuda", dtype=torch.float64)
+        loss = torch.empty(2, device="cuda", dtype=torch.float64)
+        pose = cams.poses[0]
+        plx.render_backward_pose(grid, cams, 0, o, rgb_t, depth_t, out=(H, b, loss))
+        plx.pose_step(H, b, pose)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(iters):
+                plx.render_backward_pose(grid, cams, 0, o, rgb_t, depth_t, out=(H, b, loss))
+                plx.pose_step(H, b, pose)
+        for _ in range(args.warmup):
+            cams.poses.copy_(start)
+            g.replay()
+        barrier()
+        evs = []
+        for _ in range(max(1, args.steps // 2)):
+            cams.poses.copy_(start)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            evs.append((e0, e1))
+        barrier()
+        ms = [a.elapsed_time(b_) for a, b_ in evs]
+        err = float(np.abs(pose.cpu().numpy().reshape(3, 4) - cam.T_wc).max())
+        out[storage] = {"value": iters * len(ms) / (sum(ms) / 1e3),
+                        "ms_per_iter": sum(ms) / len(ms) / iters,
+                        "final_pose_err": err, "final_loss": float(loss[0].item())}
+        grid.close()
+    out["value"] = out["f32"]["value"]
+    return out
+
+
+# ---------------------------------------------------------- CPU baselines
+def cpu_baseline(sc, cams, rgb_np, depth_np, opts, seconds):
+    """The FP64 oracle (as it stands) on seeded chunks of 2048 of the workload's
+    rays, repeated until ``seconds`` of wall time have passed."""
+    import oracle
+    from oracle import build as obuild
+
+    from paper_2307_03404_b300 import scenes
+
+    obuild.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    offs = np.cumsum([0] + [c.width * c.height for c in cams])[:-1]
+    done, t0, i = 0, time.time(), 0
+    while time.time() - t0 < seconds:
+        cid, pix = scenes.random_rays(cams, 2048, 12345 + i)
+        rows = offs[cid] + pix
+        oracle.grad_grid(sc.grid, cams, opts, rgb_np[rows], depth_np[rows], rays=(cid, pix))
+        done += 2048
+        i += 1
+    dt = time.time() - t0
+    return {"value": done / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} seeded random rays of the same 8 keyframes in chunks of 2048 "
+                      f"(forward + loss + grid gradient, FP64, OpenMP over rays), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, same metric/config."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from oracle import build as obuild
+
+    from paper_2307_03404_b300 import scenes
+
+    obuild.build()
+    sc, cams, rgb_np, depth_np, opts = mapping_workload(1, 0)
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    n = args.cpu_rays_per_step
+    offs = np.cumsum([0] + [c.width * c.height for c in cams])[:-1]
+
+    def one(i):
+        cid, pix = scenes.random_rays(cams, n, 777 + i)
+        rows = offs[cid] + pix
+        oracle.grad_grid(sc.grid, cams, opts, rgb_np[rows], depth_np[rows], rays=(cid, pix))
+
+    for i in range(args.warmup):
+        one(i)
+    t = time.time()
+    for i in range(args.steps):
+        one(100 + i)
+    dt = time.time() - t
+    value = n * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": dict(workload_config(sc, cams, "f64"), parallelism="host cores"),
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step {n} seeded random rays of the workload"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16", "f32_bf16"])
+    ap.add_argument("--tracking-workload", default="room512")
+    ap.add_argument("--tracking-iters", type=int, default=100)
+    ap.add_argument("--no-tracking", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-rays-per-step", type=int, default=512)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("[bench] warmup raised to 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * plx.h - C ABI of the B300 (sm_103a) Plenoxel RGB-D renderer.
+ *
+ * The library renders rays through a sparse voxel grid and differentiates the
+ * result, following "RGB-D Mapping and Tracking in a Plenoxel Radiance Field"
+ * (arXiv 2307.03404):
+ *   - forward render: Sec. 4, Eq. 1 (colour), Eq. 2 (transmittance), Eq. 3
+ *     (expected depth), on the grid of Sec. 5.2 (28 values per vertex,
+ *     trilinear interpolation);
+ *   - mapping adjoint: Sec. 5.2, Eq. 4-11 (loss and its gradient to the grid);
+ *   - tracking: Sec. 5.3, Eq. 12-14 and Appendix A (gradient of the rendered
+ *     colour and depth with respect to the camera pose), reduced to a
+ *     Gauss-Newton system and stepped on SE(3).
+ *
+ * Conventions common to every call
+ *   - Every function returns a plx_status. On failure plx_last_error() gives a
+ *     message (thread-local, valid until the next call on the same thread).
+ *     No C++ exception crosses this boundary.
+ *   - Array pointers are DEVICE pointers owned by the caller unless a comment
+ *     says HOST. Descriptor structs (plx_grid_desc, plx_cameras, plx_rays,
+ *     plx_render_opts) are HOST memory, read during the call only.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream. Every call is asynchronous on its stream, except
+ *     plx_grid_create / plx_grid_destroy / plx_grid_check, which synchronise.
+ *     No call synchronises the device or allocates memory except those three,
+ *     so the render, backward and pose-step calls can be captured in a CUDA
+ *     graph.
+ *   - A grid handle owns scratch memory: calls that use one handle must not
+ *     run concurrently on different streams.
+ *
+ * Geometry
+ *   - Grid: res[0..2] vertices along x, y, z spanning the box [lo, hi];
+ *     vertex (x, y, z) sits at lo + (x, y, z) * h with h = (hi - lo)/(res - 1).
+ *   - Camera: pinhole, pixel (u, v) has centre (u + 1/2, v + 1/2); camera
+ *     frame x right, y down, z forward; pose = camera-to-world [R | o] as a
+ *     row-major 3x4 array of doubles. The ray of pixel (u, v) is o + t d with
+ *     d = R d_c / |d_c|, d_c = ((u + 1/2 - cx)/fx, (v + 1/2 - cy)/fy, 1).
+ *   - Samples: with [t_min, t_max] the overlap of the ray with the grid box
+ *     (t_min no smaller than near_t), sample k sits at
+ *     t_k = t_min + (k + 1/2) * step for k < floor((t_max - t_min)/step),
+ *     at most max_samples; every delta_k is `step`.
+ *   - Activations: sigma = max(0, trilinear density); colour = sigmoid (or
+ *     identity) of sum_k Y_k(d) * trilinear SH_k, Y the real SH of degree
+ *     0..2 in the order (1; y, z, x; xy, yz, 3z^2-1, xz, x^2-y^2).
+ *   - Rendered colour includes the background term T_{N+1} * bg.
+ *   - Depth targets are sensor z-depths (depth_is_z = 1, converted to ray
+ *     distance by |d_c|) or ray distances (depth_is_z = 0). A ray whose depth
+ *     target is not positive or not finite is left out of the losses and of
+ *     their normaliser M (Sec. 6.1: invalid depth pixels are disregarded).
+ */
+#ifndef PLX_H
+#define PLX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PLX_OK = 0,
+  PLX_EINVAL = 1,        /* bad argument (null pointer, size, range) */
+  PLX_ENOMEM = 2,        /* device allocation failed */
+  PLX_ECUDA = 3,         /* a CUDA runtime call failed */
+  PLX_EDEVICE_CHECK = 4, /* a device-side check failed (see plx_grid_check) */
+  PLX_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  PLX_EUNSUPPORTED = 6   /* option not supported by this build */
+} plx_status;
+
+/* Storage of the 28 values of a vertex inside the library. Every mode
+ * computes in FP32; the 16-bit modes halve the bytes gathered per sample. */
+typedef enum {
+  PLX_STORE_F32 = 0,      /* density and SH in FP32 (128-byte record) */
+  PLX_STORE_BF16 = 1,     /* density and SH in BF16 (64-byte record) */
+  PLX_STORE_F16 = 2,      /* density and SH in FP16 (64-byte record) */
+  PLX_STORE_F32_BF16 = 3  /* density FP32, SH BF16 (64-byte record) */
+} plx_storage;
+
+typedef enum { PLX_ACT_SIGMOID = 0, PLX_ACT_IDENTITY = 1 } plx_color_act;
+
+#define PLX_MAX_CAMERAS 128
+#define PLX_GRAD_STRIDE 32 /* floats per vertex in gradient buffers */
+
+typedef struct {
+  int32_t res[3];     /* vertices along x, y, z; each >= 2 */
+  double lo[3];       /* box corner of vertex (0, 0, 0), world units */
+  double hi[3];       /* box corner of vertex (res-1), world units; hi > lo */
+  int64_t n_alloc;    /* allocated vertices (rows of density / sh) */
+  int32_t storage;    /* plx_storage */
+  int32_t reserved;
+} plx_grid_desc;
+
+typedef struct plx_grid plx_grid; /* opaque */
+
+typedef struct {
+  double fx, fy, cx, cy; /* pixels */
+  int32_t width, height; /* pixels; width * height < 2^31 */
+} plx_intrinsics;
+
+typedef struct {
+  int32_t n_cams;              /* 1 .. PLX_MAX_CAMERAS */
+  int32_t reserved;
+  const plx_intrinsics *intr;  /* HOST [n_cams] */
+  const double *poses;         /* DEVICE [n_cams][12] camera-to-world [R | o] */
+} plx_cameras;
+
+/* Which rays a call processes.
+ * Dense mode (cam_id == NULL and pixel == NULL): every pixel of every camera,
+ *   camera after camera, row-major inside a camera; ray index r of pixel
+ *   (u, v) of camera c is (sum of W*H of cameras before c) + v*W + u, and
+ *   n_rays must be 0 or that total.
+ * List mode (pixel != NULL): n_rays rays, ray i is pixel[i] = v*W + u of
+ *   camera cam_id[i] (cam_id may be NULL when there is one camera). */
+typedef struct {
+  int64_t n_rays;
+  const int32_t *cam_id; /* DEVICE [n_rays] or NULL */
+  const int32_t *pixel;  /* DEVICE [n_rays] or NULL */
+} plx_rays;
+
+typedef struct {
+  double step;         /* sample spacing delta in world units, > 0 */
+  double near_t;       /* smallest t marched, >= 0 */
+  double stop_T;       /* stop a ray once T_{i+1} < stop_T; 0 = never */
+  float bg[3];         /* background colour */
+  float lambda_d;      /* lambda_d of Eq. 11, >= 0 */
+  int32_t max_samples; /* cap on samples per ray, >= 0 */
+  int32_t color_act;   /* plx_color_act */
+  int32_t depth_is_z;  /* 1: depth targets are z-depths; 0: ray distances */
+  int32_t reserved;
+} plx_render_opts;
+
+const char *plx_last_error(void);
+const char *plx_version(void);
+
+/* Sec. 5.2 (model representation), Sec. 6.1 (sparse grid up to 512^3).
+ * Copies a grid given in the canonical layout into library-owned device
+ * memory in the storage format desc->storage (16-bit modes round to nearest
+ * even), builds the empty-cell occupancy it marches with, and checks every
+ * link.
+ *   links   DEVICE int32 [res_z][res_y][res_x]; -1 or 0 .. n_alloc-1
+ *   density DEVICE float [n_alloc]
+ *   sh      DEVICE float [n_alloc][27], channel-major (R0..R8, G0..G8, B0..B8)
+ * Synchronises `stream`. Errors: PLX_EINVAL (descriptor, or a link out of
+ * range), PLX_ENOMEM, PLX_ECUDA. On success *out owns the copy; the caller's
+ * arrays may be freed. */
+plx_status plx_grid_create(const plx_grid_desc *desc, const int32_t *links,
+                           const float *density, const float *sh, void *stream,
+                           plx_grid **out);
+
+/* Replace every density / SH value (same layout as plx_grid_create; links
+ * unchanged), e.g. after an optimiser step. Asynchronous. */
+plx_status plx_grid_upload(plx_grid *grid, const float *density,
+                           const float *sh, void *stream);
+
+/* Copy the stored values back to the canonical layout (FP32; 16-bit storage
+ * is widened exactly). Asynchronous. */
+plx_status plx_grid_download(const plx_grid *grid, float *density, float *sh,
+                             void *stream);
+
+/* Descriptor of a grid (HOST out). */
+plx_status plx_grid_info(const plx_grid *grid, plx_grid_desc *out);
+
+/* Frees the grid's device memory (synchronises the device first). */
+plx_status plx_grid_destroy(plx_grid *grid);
+
+/* Sec. 4, Eq. 1-3. Renders every ray of `rays`.
+ *   rgb_out   DEVICE float [n_rays][3]  rendered colour C (incl. background)
+ *   depth_out DEVICE float [n_rays]     expected depth D (ray distance)
+ *   state_out DEVICE float [n_rays]     final transmittance T_{N+1}, or NULL
+ *   counts_out DEVICE int32 [n_rays][2] samples marched and samples with an
+ *             allocated corner, or NULL (counting costs a little time)
+ * Output row r is ray r (see plx_rays). Errors: PLX_EINVAL, PLX_ECUDA. */
+plx_status plx_render_forward(const plx_grid *grid, const plx_cameras *cams,
+                              const plx_rays *rays, const plx_render_opts *opts,
+                              float *rgb_out, float *depth_out, float *state_out,
+                              int32_t *counts_out, void *stream);
+
+/* Sec. 5.2, Eq. 4-11. Mapping adjoint: for the loss
+ *   L = 1/M sum_valid |C - C_t|^2 + lambda_d/M sum_valid (D - D_t)^2
+ * re-marches every valid ray, recomputes T_i and the prefix sums of Eq. 9-10
+ * (nothing per sample is stored by the forward), and ADDS dL/d(value) into
+ * `grad`.
+ *   rgb_target   DEVICE float [n_rays][3]
+ *   depth_target DEVICE float [n_rays] (see depth_is_z)
+ *   rgb, depth   DEVICE float, the outputs of plx_render_forward for the
+ *                same grid, cameras, rays and opts
+ *   grad         DEVICE float [n_alloc][PLX_GRAD_STRIDE], 16-byte aligned:
+ *                slot 0 = dL/d density, slots 1..27 = dL/d SH (canonical
+ *                order), slots 28..31 untouched. The caller zeroes it.
+ *   loss_out     DEVICE double [2] or NULL: overwritten with (L, M).
+ * Errors: PLX_EINVAL, PLX_ECUDA. */
+plx_status plx_render_backward_grid(const plx_grid *grid,
+                                    const plx_cameras *cams,
+                                    const plx_rays *rays,
+                                    const plx_render_opts *opts,
+                                    const float *rgb_target,
+                                    const float *depth_target, const float *rgb,
+                                    const float *depth, float *grad,
+                                    double *loss_out, void *stream);
+
+/* Sec. 5.3, Eq. 12-14, Appendix A. Tracking: for the rays of camera `cam`
+ * (dense mode: all its pixels; list mode: pixel[] of that camera, cam_id
+ * ignored) computes the 4x6 Jacobian of (C - C_t, D - D_t) with respect to
+ * a left perturbation xi = (rho, phi) of the pose, T <- exp(xi^) T, with t_i,
+ * delta_i and the SH direction held fixed as in the paper, and reduces it in
+ * FP64 over the valid rays with W = diag(1, 1, 1, lambda_d) / M:
+ *   JtWJ DEVICE double [36] = sum J^T W J (row-major, symmetric)
+ *   JtWr DEVICE double [6]  = sum J^T W r
+ *   loss DEVICE double [2]  = (sum r^T W r, M)
+ * All three are overwritten. The reduction order is fixed, so the result is
+ * deterministic. Targets are indexed like the rays. */
+plx_status plx_render_backward_pose(const plx_grid *grid,
+                                    const plx_cameras *cams, int32_t cam,
+                                    const plx_rays *rays,
+                                    const plx_render_opts *opts,
+                                    const float *rgb_target,
+                                    const float *depth_target, double *JtWJ,
+                                    double *JtWr, double *loss, void *stream);
+
+/* Sec. 5.3 (the pose is optimised directly). Gauss-Newton step, on the
+ * device in FP64: solves (JtWJ + damping I) xi = -JtWr by Cholesky and sets
+ * pose <- exp(xi^) pose (SE(3) exponential: Rodrigues rotation, V rho
+ * translation).
+ *   pose    DEVICE double [12], updated in place (e.g. plx_cameras.poses + 12c)
+ *   xi_out  DEVICE double [6] or NULL
+ *   status  DEVICE int32 [1] or NULL: 0, or 1 when the damped system is not
+ *           positive definite (the pose is then left unchanged)
+ * Asynchronous; graph-capturable. */
+plx_status plx_pose_step(const double *JtWJ, const double *JtWr, double damping,
+                         double *pose, double *xi_out, int32_t *status,
+                         void *stream);
+
+/* Reads and clears the grid's device error word (synchronises `stream`).
+ * Returns PLX_EDEVICE_CHECK if a device-side check failed since the last
+ * call. */
+plx_status plx_grid_check(const plx_grid *grid, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLX_H */

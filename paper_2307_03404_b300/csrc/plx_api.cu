@@ -1,0 +1,427 @@
+// C ABI of the renderer: argument checks, grid ownership and layout, launch
+// parameter set-up. Every compute step runs in the kernels of plx_render.cu
+// and plx_pose.cu; this file only validates, allocates (grid create/destroy)
+// and launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "plx_internal.cuh"
+
+namespace plx {
+void launch_forward(int store, const Common& P, float* rgb, float* depth, float* state,
+                    int32_t* counts, cudaStream_t s);
+void launch_backward_grid(int store, const Common& P, const float* rgb_t, const float* depth_t,
+                          const float* rgb, const float* depth, float* grad, double* loss_out,
+                          unsigned long long* M, int num_sms, cudaStream_t s);
+void launch_backward_pose(int store, const Common& P, const float* rgb_t, const float* depth_t,
+                          double* partials, unsigned* retire, double* JtWJ, double* JtWr,
+                          double* loss, int max_blocks, cudaStream_t s);
+void launch_pose_step(const double* H, const double* b, double damping, double* pose,
+                      double* xi_out, int32_t* status, cudaStream_t s);
+int pose_kernel_blocks_per_sm(int store);
+}  // namespace plx
+
+using namespace plx;
+
+// Scratch owned by a grid handle (device memory).
+struct Workspace {
+  int32_t err;                    // device error word
+  unsigned int retire;            // pose-reduction retirement counter
+  unsigned long long M;           // valid-ray count of the last backward call
+  unsigned long long pad[5];
+  // followed by double partials[max_blocks][32]
+};
+
+struct plx_grid {
+  plx_grid_desc desc;
+  int32_t* links = nullptr;
+  void* rec = nullptr;
+  int rec_bytes = 0;
+  char* ws = nullptr;
+  int max_pose_blocks = 0;
+  int num_sms = 0;
+  int device = 0;
+  double inv_h[3];
+};
+
+static thread_local std::string g_err;
+
+static plx_status fail(plx_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                               \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(e_ == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                    \
+  } while (0)
+
+static plx_status launch_check(const char* what) {
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PLX_ECUDA, "%s: launch failed: %s", what, cudaGetErrorString(e));
+  }
+  return PLX_OK;
+}
+
+static int record_bytes(int storage) { return storage == PLX_STORE_F32 ? 128 : 64; }
+
+// ----------------------------------------------------------- repack kernels
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+  return lo | (hi << 16);
+}
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+  const uint32_t lo = __half_as_ushort(__float2half_rn(a));
+  const uint32_t hi = __half_as_ushort(__float2half_rn(b));
+  return lo | (hi << 16);
+}
+
+__global__ void k_repack(const float* __restrict__ density, const float* __restrict__ sh,
+                         int64_t n, int storage, void* __restrict__ rec) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float v[32];
+    v[0] = density[i];
+    for (int j = 0; j < 27; ++j) v[1 + j] = sh[i * 27 + j];
+    for (int j = 28; j < 32; ++j) v[j] = 0.f;
+    if (storage == PLX_STORE_F32) {
+      float4* d = reinterpret_cast<float4*>(rec) + i * 8;
+      for (int j = 0; j < 8; ++j) d[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    } else {
+      uint32_t w[16];
+      if (storage == PLX_STORE_BF16) {
+        for (int j = 0; j < 16; ++j) w[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+      } else if (storage == PLX_STORE_F16) {
+        for (int j = 0; j < 16; ++j) w[j] = pack_f16(v[2 * j], v[2 * j + 1]);
+      } else {
+        w[0] = __float_as_uint(v[0]);
+        for (int j = 0; j < 15; ++j) w[j + 1] = pack_bf16(v[1 + 2 * j], v[2 + 2 * j]);
+      }
+      uint4* d = reinterpret_cast<uint4*>(rec) + i * 4;
+      for (int j = 0; j < 4; ++j) d[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+    }
+  }
+}
+
+__global__ void k_unpack(const void* __restrict__ rec, int64_t n, int storage,
+                         float* __restrict__ density, float* __restrict__ sh) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float v[28];
+    switch (storage) {
+      case PLX_STORE_F32: load_record<PLX_STORE_F32>(rec, (int32_t)i, v); break;
+      case PLX_STORE_BF16: load_record<PLX_STORE_BF16>(rec, (int32_t)i, v); break;
+      case PLX_STORE_F16: load_record<PLX_STORE_F16>(rec, (int32_t)i, v); break;
+      default: load_record<PLX_STORE_F32_BF16>(rec, (int32_t)i, v); break;
+    }
+    density[i] = v[0];
+    for (int j = 0; j < 27; ++j) sh[i * 27 + j] = v[1 + j];
+  }
+}
+
+__global__ void k_check_links(const int32_t* __restrict__ links, int64_t n, int64_t n_alloc,
+                              int32_t* __restrict__ err) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = links[i];
+    bad |= l < -1 || (int64_t)l >= n_alloc;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 2);
+}
+
+static unsigned grid_stride_blocks(int64_t n, int num_sms) {
+  const int64_t want = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms * 8;
+  return (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+// ------------------------------------------------------------------- ABI
+extern "C" {
+
+const char* plx_last_error(void) { return g_err.c_str(); }
+
+const char* plx_version(void) { return "plx 0.1 sm_103a"; }
+
+plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, const float* density,
+                           const float* sh, void* stream, plx_grid** out) {
+  if (!desc || !out) return fail(PLX_EINVAL, "grid_create: null desc or out");
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a) {
+    if (desc->res[a] < 2 || desc->res[a] > 65536)
+      return fail(PLX_EINVAL, "grid_create: res[%d] = %d out of [2, 65536]", a, desc->res[a]);
+    if (!(desc->hi[a] > desc->lo[a]) || !std::isfinite(desc->lo[a]) || !std::isfinite(desc->hi[a]))
+      return fail(PLX_EINVAL, "grid_create: need lo < hi on axis %d", a);
+  }
+  if (desc->n_alloc < 0 || desc->n_alloc > INT32_MAX)
+    return fail(PLX_EINVAL, "grid_create: n_alloc %lld out of range", (long long)desc->n_alloc);
+  if (desc->storage < PLX_STORE_F32 || desc->storage > PLX_STORE_F32_BF16)
+    return fail(PLX_EINVAL, "grid_create: unknown storage %d", desc->storage);
+  if (!links) return fail(PLX_EINVAL, "grid_create: null links");
+  if (desc->n_alloc > 0 && (!density || !sh))
+    return fail(PLX_EINVAL, "grid_create: null density or sh");
+  const int64_t n_links = (int64_t)desc->res[0] * desc->res[1] * desc->res[2];
+  cudaStream_t s = (cudaStream_t)stream;
+
+  plx_grid* g = new plx_grid();
+  g->desc = *desc;
+  g->rec_bytes = record_bytes(desc->storage);
+  for (int a = 0; a < 3; ++a) g->inv_h[a] = (double)(desc->res[a] - 1) / (desc->hi[a] - desc->lo[a]);
+  auto cleanup = [&](plx_status st) {
+    cudaFree(g->links);
+    cudaFree(g->rec);
+    cudaFree(g->ws);
+    delete g;
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (e != cudaSuccess) return cleanup(fail(PLX_ECUDA, "grid_create: %s", cudaGetErrorString(e)));
+  int bps = 1;
+  for (int st = 0; st < 4; ++st) {
+    const int b = pose_kernel_blocks_per_sm(st);
+    bps = b > bps ? b : bps;
+  }
+  g->max_pose_blocks = g->num_sms * bps;
+  const size_t ws_bytes = sizeof(Workspace) + (size_t)g->max_pose_blocks * 32 * sizeof(double);
+  e = cudaMalloc(&g->links, (size_t)n_links * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->rec, (size_t)(desc->n_alloc > 0 ? desc->n_alloc : 1) * g->rec_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->ws, ws_bytes);
+  if (e != cudaSuccess)
+    return cleanup(fail(e == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA,
+                        "grid_create: allocation failed: %s", cudaGetErrorString(e)));
+  e = cudaMemsetAsync(g->ws, 0, ws_bytes, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->links, links, (size_t)n_links * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cleanup(fail(PLX_ECUDA, "grid_create: %s", cudaGetErrorString(e)));
+  Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
+  k_check_links<<<grid_stride_blocks(n_links, g->num_sms), 256, 0, s>>>(g->links, n_links,
+                                                                      desc->n_alloc, &ws->err);
+  if (desc->n_alloc > 0)
+    k_repack<<<grid_stride_blocks(desc->n_alloc, g->num_sms), 256, 0, s>>>(
+        density, sh, desc->n_alloc, desc->storage, g->rec);
+  if (launch_check("grid_create") != PLX_OK) return cleanup(PLX_ECUDA);
+  int32_t err = 0;
+  e = cudaMemcpyAsync(&err, &ws->err, sizeof(err), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cleanup(fail(PLX_ECUDA, "grid_create: %s", cudaGetErrorString(e)));
+  if (err) return cleanup(fail(PLX_EINVAL, "grid_create: a link is outside [-1, n_alloc)"));
+  *out = g;
+  return PLX_OK;
+}
+
+plx_status plx_grid_upload(plx_grid* g, const float* density, const float* sh, void* stream) {
+  if (!g) return fail(PLX_EINVAL, "grid_upload: null grid");
+  if (g->desc.n_alloc == 0) return PLX_OK;
+  if (!density || !sh) return fail(PLX_EINVAL, "grid_upload: null density or sh");
+  k_repack<<<grid_stride_blocks(g->desc.n_alloc, g->num_sms), 256, 0, (cudaStream_t)stream>>>(
+      density, sh, g->desc.n_alloc, g->desc.storage, g->rec);
+  return launch_check("grid_upload");
+}
+
+plx_status plx_grid_download(const plx_grid* g, float* density, float* sh, void* stream) {
+  if (!g) return fail(PLX_EINVAL, "grid_download: null grid");
+  if (g->desc.n_alloc == 0) return PLX_OK;
+  if (!density || !sh) return fail(PLX_EINVAL, "grid_download: null density or sh");
+  k_unpack<<<grid_stride_blocks(g->desc.n_alloc, g->num_sms), 256, 0, (cudaStream_t)stream>>>(
+      g->rec, g->desc.n_alloc, g->desc.storage, density, sh);
+  return launch_check("grid_download");
+}
+
+plx_status plx_grid_info(const plx_grid* g, plx_grid_desc* out) {
+  if (!g || !out) return fail(PLX_EINVAL, "grid_info: null argument");
+  *out = g->desc;
+  return PLX_OK;
+}
+
+plx_status plx_grid_destroy(plx_grid* g) {
+  if (!g) return PLX_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(g->links);
+  cudaFree(g->rec);
+  cudaFree(g->ws);
+  delete g;
+  if (e != cudaSuccess) return fail(PLX_ECUDA, "grid_destroy: %s", cudaGetErrorString(e));
+  return PLX_OK;
+}
+
+plx_status plx_grid_check(const plx_grid* g, void* stream) {
+  if (!g) return fail(PLX_EINVAL, "grid_check: null grid");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
+  int32_t err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, &ws->err, sizeof(err), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemsetAsync(&ws->err, 0, sizeof(int32_t), s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (err & 1) return fail(PLX_EDEVICE_CHECK, "a ray list held a camera or pixel out of range");
+  if (err) return fail(PLX_EDEVICE_CHECK, "device check failed (code %d)", err);
+  return PLX_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ call set-up
+static plx_status build_common(const char* what, const plx_grid* g, const plx_cameras* cams,
+                               const plx_rays* rays, const plx_render_opts* o, int32_t fixed_cam,
+                               Common& P) {
+  if (!g || !cams || !rays || !o) return fail(PLX_EINVAL, "%s: null argument", what);
+  if (cams->n_cams < 1 || cams->n_cams > PLX_MAX_CAMERAS)
+    return fail(PLX_EINVAL, "%s: n_cams %d out of [1, %d]", what, cams->n_cams, PLX_MAX_CAMERAS);
+  if (!cams->intr || !cams->poses) return fail(PLX_EINVAL, "%s: null intrinsics or poses", what);
+  if (!(o->step > 0.0) || !std::isfinite(o->step))
+    return fail(PLX_EINVAL, "%s: step must be > 0", what);
+  if (!(o->near_t >= 0.0) || !(o->stop_T >= 0.0) || o->max_samples < 0 || !(o->lambda_d >= 0.f))
+    return fail(PLX_EINVAL, "%s: near_t, stop_T, max_samples, lambda_d must be >= 0", what);
+  if (o->color_act != PLX_ACT_SIGMOID && o->color_act != PLX_ACT_IDENTITY)
+    return fail(PLX_EINVAL, "%s: unknown color_act %d", what, o->color_act);
+  if (fixed_cam >= cams->n_cams) return fail(PLX_EINVAL, "%s: cam %d out of range", what, fixed_cam);
+  std::memset(&P, 0, sizeof(P));
+  P.g.links = g->links;
+  P.g.rec = g->rec;
+  P.g.rx = g->desc.res[0];
+  P.g.ry = g->desc.res[1];
+  P.g.rz = g->desc.res[2];
+  P.g.n_alloc = (int32_t)g->desc.n_alloc;
+  for (int a = 0; a < 3; ++a) {
+    P.g.lo[a] = g->desc.lo[a];
+    P.g.hi[a] = g->desc.hi[a];
+    P.g.inv_h[a] = g->inv_h[a];
+  }
+  P.o.step = o->step;
+  P.o.near_t = o->near_t;
+  P.o.stop_T = (float)o->stop_T;
+  P.o.step_f = (float)o->step;
+  for (int c = 0; c < 3; ++c) P.o.bg[c] = o->bg[c];
+  P.o.lambda_d = o->lambda_d;
+  P.o.max_samples = o->max_samples;
+  P.o.color_act = o->color_act;
+  P.o.depth_is_z = o->depth_is_z;
+  P.poses = cams->poses;
+  P.err = &reinterpret_cast<Workspace*>(g->ws)->err;
+  P.ct.n_cams = cams->n_cams;
+  int64_t ray_off = 0, tile_off = 0;
+  for (int c = 0; c < cams->n_cams; ++c) {
+    const plx_intrinsics& in = cams->intr[c];
+    if (in.width < 1 || in.height < 1 || (int64_t)in.width * in.height >= (1ll << 31))
+      return fail(PLX_EINVAL, "%s: camera %d size %dx%d", what, c, in.width, in.height);
+    if (!(in.fx != 0.0) || !(in.fy != 0.0) || !std::isfinite(in.fx) || !std::isfinite(in.fy))
+      return fail(PLX_EINVAL, "%s: camera %d focal length", what, c);
+    CamParam& cp = P.ct.cam[c];
+    cp.inv_fx = 1.0 / in.fx;
+    cp.inv_fy = 1.0 / in.fy;
+    cp.cx = in.cx;
+    cp.cy = in.cy;
+    cp.width = in.width;
+    cp.height = in.height;
+    cp.tiles_x = (in.width + kTileW - 1) / kTileW;
+    const int tiles_y = (in.height + kTileH - 1) / kTileH;
+    const bool use = fixed_cam < 0 || fixed_cam == c;
+    cp.ray_off = ray_off;
+    cp.tile_off = tile_off;
+    if (use) {
+      ray_off += (int64_t)in.width * in.height;
+      tile_off += (int64_t)cp.tiles_x * tiles_y;
+    }
+  }
+  const bool dense = rays->pixel == nullptr;
+  if (dense && rays->cam_id)
+    return fail(PLX_EINVAL, "%s: cam_id given without pixel", what);
+  P.rl.cam_id = rays->cam_id;
+  P.rl.pixel = rays->pixel;
+  P.rl.fixed_cam = fixed_cam;
+  P.ct.dense = dense ? 1 : 0;
+  if (dense) {
+    if (fixed_cam >= 0) {  // only camera `fixed_cam` is marched; its rays start at 0
+      P.ct.cam[fixed_cam].tile_off = 0;
+      P.ct.cam[fixed_cam].ray_off = 0;
+    }
+    if (rays->n_rays != 0 && rays->n_rays != ray_off)
+      return fail(PLX_EINVAL, "%s: dense mode covers %lld rays, n_rays = %lld", what,
+                  (long long)ray_off, (long long)rays->n_rays);
+    P.ct.n_rays = ray_off;
+    P.ct.n_tiles = tile_off;
+  } else {
+    if (rays->n_rays < 0) return fail(PLX_EINVAL, "%s: n_rays < 0", what);
+    if (!rays->cam_id && cams->n_cams > 1 && fixed_cam < 0)
+      return fail(PLX_EINVAL, "%s: cam_id needed with several cameras", what);
+    P.ct.n_rays = rays->n_rays;
+    P.ct.n_tiles = (rays->n_rays + 31) / 32;
+  }
+  return PLX_OK;
+}
+
+extern "C" {
+
+plx_status plx_render_forward(const plx_grid* g, const plx_cameras* cams, const plx_rays* rays,
+                              const plx_render_opts* opts, float* rgb_out, float* depth_out,
+                              float* state_out, int32_t* counts_out, void* stream) {
+  Common P;
+  plx_status st = build_common("render_forward", g, cams, rays, opts, -1, P);
+  if (st != PLX_OK) return st;
+  if (P.ct.n_rays > 0 && (!rgb_out || !depth_out))
+    return fail(PLX_EINVAL, "render_forward: null rgb_out or depth_out");
+  launch_forward(g->desc.storage, P, rgb_out, depth_out, state_out, counts_out,
+                 (cudaStream_t)stream);
+  return launch_check("render_forward");
+}
+
+plx_status plx_render_backward_grid(const plx_grid* g, const plx_cameras* cams,
+                                    const plx_rays* rays, const plx_render_opts* opts,
+                                    const float* rgb_target, const float* depth_target,
+                                    const float* rgb, const float* depth, float* grad,
+                                    double* loss_out, void* stream) {
+  Common P;
+  plx_status st = build_common("render_backward_grid", g, cams, rays, opts, -1, P);
+  if (st != PLX_OK) return st;
+  if (P.ct.n_rays > 0 && (!rgb_target || !depth_target || !rgb || !depth || !grad))
+    return fail(PLX_EINVAL, "render_backward_grid: null array argument");
+  if (reinterpret_cast<uintptr_t>(grad) % 16 != 0)
+    return fail(PLX_EINVAL, "render_backward_grid: grad must be 16-byte aligned");
+  Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
+  launch_backward_grid(g->desc.storage, P, rgb_target, depth_target, rgb, depth, grad, loss_out,
+                       &ws->M, g->num_sms, (cudaStream_t)stream);
+  return launch_check("render_backward_grid");
+}
+
+plx_status plx_render_backward_pose(const plx_grid* g, const plx_cameras* cams, int32_t cam,
+                                    const plx_rays* rays, const plx_render_opts* opts,
+                                    const float* rgb_target, const float* depth_target,
+                                    double* JtWJ, double* JtWr, double* loss, void* stream) {
+  if (cam < 0) return fail(PLX_EINVAL, "render_backward_pose: cam < 0");
+  Common P;
+  plx_status st = build_common("render_backward_pose", g, cams, rays, opts, cam, P);
+  if (st != PLX_OK) return st;
+  if (!JtWJ || !JtWr || !loss) return fail(PLX_EINVAL, "render_backward_pose: null output");
+  if (P.ct.n_rays > 0 && (!rgb_target || !depth_target))
+    return fail(PLX_EINVAL, "render_backward_pose: null target");
+  Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
+  double* partials = reinterpret_cast<double*>(g->ws + sizeof(Workspace));
+  launch_backward_pose(g->desc.storage, P, rgb_target, depth_target, partials, &ws->retire, JtWJ,
+                       JtWr, loss, g->max_pose_blocks, (cudaStream_t)stream);
+  return launch_check("render_backward_pose");
+}
+
+plx_status plx_pose_step(const double* JtWJ, const double* JtWr, double damping, double* pose,
+                         double* xi_out, int32_t* status, void* stream) {
+  if (!JtWJ || !JtWr || !pose) return fail(PLX_EINVAL, "pose_step: null argument");
+  if (!(damping >= 0.0) || !std::isfinite(damping))
+    return fail(PLX_EINVAL, "pose_step: damping must be finite and >= 0");
+  launch_pose_step(JtWJ, JtWr, damping, pose, xi_out, status, (cudaStream_t)stream);
+  return launch_check("pose_step");
+}
+
+}  // extern "C"

@@ -1,0 +1,361 @@
+// Device-side building blocks of the sm_103a Plenoxel renderer.
+//
+// One thread marches one ray; a warp owns an 8x4 pixel tile in dense mode so
+// that its rays stay close in space and share cached grid lines. Per ray the
+// geometry is set up once in FP64 (ray direction, box clip, grid-space origin)
+// and handed to the sample loop as float-float pairs, so that sample positions
+// keep ~1e-7 voxel accuracy on 1024^3 grids while the loop itself runs in
+// FP32 only. The 8 corner records of the current cell are cached in registers
+// as (density, SH projected on the ray's direction per channel): the SH basis
+// of Sec. 5.2 depends on the ray only, so sum_k Y_k trilerp(SH_k) equals
+// trilerp(sum_k Y_k SH_k) and a cell visit costs 8 record loads while each
+// sample costs 32 FMAs.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plx.h"
+
+namespace plx {
+
+constexpr int kTileW = 8;             // dense-mode warp tile: 8 x 4 pixels
+constexpr int kTileH = 4;
+constexpr int kBlock = 256;           // threads per block of the ray kernels
+constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr int kRecordSlots = 32;      // record = 32 slots (28 used)
+
+// ---------------------------------------------------------------- params
+struct CamParam {
+  double inv_fx, inv_fy, cx, cy;  // 1/fx, 1/fy, principal point
+  int32_t width, height;
+  int64_t ray_off;                // dense mode: index of the camera's ray 0
+  int64_t tile_off;               // dense mode: index of the camera's tile 0
+  int32_t tiles_x;                // tiles per row
+  int32_t pad;
+};
+
+struct CamTable {
+  int32_t n_cams;
+  int32_t dense;                  // 1: every pixel of every camera
+  int64_t n_rays;
+  int64_t n_tiles;                // dense: 8x4 tiles; list: ceil(n_rays / 32)
+  CamParam cam[PLX_MAX_CAMERAS];
+};
+
+struct RayList {
+  const int32_t* cam_id;          // list mode, may be null (single camera)
+  const int32_t* pixel;           // list mode
+  int32_t fixed_cam;              // >= 0: every ray belongs to this camera
+};
+
+struct GridView {
+  const int32_t* links;           // [rz][ry][rx]
+  const void* rec;                // [n_alloc] records
+  int32_t rx, ry, rz;
+  int32_t n_alloc;
+  double lo[3];                   // box of the vertices
+  double hi[3];
+  double inv_h[3];                // 1 / spacing
+};
+
+struct Opts {
+  double step, near_t;
+  float stop_T;
+  float step_f;
+  float bg[3];
+  float lambda_d;
+  int32_t max_samples;
+  int32_t color_act;
+  int32_t depth_is_z;
+};
+
+struct Common {
+  GridView g;
+  Opts o;
+  RayList rl;
+  const double* poses;            // [n_cams][12]
+  int32_t* err;                   // device error word
+  CamTable ct;                    // last: large
+};
+
+// ----------------------------------------------------------- ray identity
+// Where the thread's ray comes from and where its outputs go.
+struct RayId {
+  int32_t cam;
+  int32_t u, v;
+  int64_t out;                    // output row
+  bool valid;
+};
+
+__device__ __forceinline__ int find_cam(const CamTable& ct, int64_t tile) {
+  int lo = 0, hi = ct.n_cams - 1;
+  while (lo < hi) {                       // last camera with tile_off <= tile
+    const int mid = (lo + hi + 1) >> 1;
+    if (ct.cam[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Ray of lane `lane` in warp-tile `tile`.
+__device__ __forceinline__ RayId ray_of(const Common& P, int64_t tile, int lane) {
+  RayId r;
+  if (P.ct.dense) {
+    const int c = P.rl.fixed_cam >= 0 ? P.rl.fixed_cam : find_cam(P.ct, tile);
+    const CamParam& cp = P.ct.cam[c];
+    const int64_t lt = tile - cp.tile_off;
+    const int ty = (int)(lt / cp.tiles_x), tx = (int)(lt - (int64_t)ty * cp.tiles_x);
+    r.cam = c;
+    r.u = tx * kTileW + (lane & (kTileW - 1));
+    r.v = ty * kTileH + (lane / kTileW);
+    r.valid = r.u < cp.width && r.v < cp.height;
+    r.out = cp.ray_off + (int64_t)r.v * cp.width + r.u;
+  } else {
+    const int64_t i = tile * 32 + lane;
+    r.valid = i < P.ct.n_rays;
+    r.out = i;
+    r.cam = 0;
+    r.u = r.v = 0;
+    if (r.valid) {
+      const int c = P.rl.fixed_cam >= 0 ? P.rl.fixed_cam
+                    : (P.rl.cam_id ? __ldg(P.rl.cam_id + i) : 0);
+      const int pix = __ldg(P.rl.pixel + i);
+      bool ok = c >= 0 && c < P.ct.n_cams;
+      if (ok) ok = pix >= 0 && pix < P.ct.cam[c].width * P.ct.cam[c].height;
+      if (!ok) {
+        r.valid = false;
+        atomicOr(P.err, 1);
+      } else {
+        r.cam = c;
+        r.u = pix % P.ct.cam[c].width;
+        r.v = pix / P.ct.cam[c].width;
+      }
+    }
+  }
+  return r;
+}
+
+// ------------------------------------------------------------ ray setup
+// Per ray, in FP64: direction, box clip, sample count, and the grid-space
+// position of sample k as b + k*s in float-float form.
+struct RayF {
+  float bh[3], bl[3];   // grid coords of sample 0: hi + lo parts
+  float sh[3], sl[3];   // grid-coord increment per sample: hi + lo parts
+  float t0, dt;         // t of sample 0, step
+  float dir[3];         // unit direction
+  float org[3];         // camera centre
+  float dc_norm;        // |d_c|
+  int n;                // samples to march
+};
+
+__device__ __forceinline__ void setup_ray(const Common& P, const RayId& id, RayF& r) {
+  const CamParam& cp = P.ct.cam[id.cam];
+  const double* T = P.poses + 12 * id.cam;
+  const double dcx = ((double)id.u + 0.5 - cp.cx) * cp.inv_fx;
+  const double dcy = ((double)id.v + 0.5 - cp.cy) * cp.inv_fy;
+  const double n2 = dcx * dcx + dcy * dcy + 1.0;
+  const double inv_n = rsqrt(n2);
+  double d[3], o[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    d[a] = (__ldg(T + 4 * a) * dcx + __ldg(T + 4 * a + 1) * dcy + __ldg(T + 4 * a + 2)) * inv_n;
+    o[a] = __ldg(T + 4 * a + 3);
+  }
+  // slab clip
+  double tn = -1e300, tf = 1e300;
+  bool hit = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] != 0.0) {
+      const double inv = 1.0 / d[a];
+      double ta = (P.g.lo[a] - o[a]) * inv, tb = (P.g.hi[a] - o[a]) * inv;
+      if (ta > tb) { const double s = ta; ta = tb; tb = s; }
+      tn = fmax(tn, ta);
+      tf = fmin(tf, tb);
+    } else if (o[a] < P.g.lo[a] || o[a] > P.g.hi[a]) {
+      hit = false;
+    }
+  }
+  tn = fmax(tn, P.o.near_t);
+  int n = 0;
+  if (hit && tf > tn) {
+    const double cnt = floor((tf - tn) / P.o.step);
+    n = (int)fmin(cnt, (double)P.o.max_samples);
+  }
+  r.n = n;
+  const double t0 = tn + 0.5 * P.o.step;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double b = (o[a] + t0 * d[a] - P.g.lo[a]) * P.g.inv_h[a];
+    const double s = P.o.step * d[a] * P.g.inv_h[a];
+    r.bh[a] = (float)b;
+    r.bl[a] = (float)(b - (double)r.bh[a]);
+    r.sh[a] = (float)s;
+    r.sl[a] = (float)(s - (double)r.sh[a]);
+    r.dir[a] = (float)d[a];
+    r.org[a] = (float)o[a];
+  }
+  r.t0 = n > 0 ? (float)t0 : 0.f;
+  r.dt = P.o.step_f;
+  r.dc_norm = (float)sqrt(n2);
+}
+
+// Real SH of degree 0..2 (orthonormal; order 1; y, z, x; xy, yz, 3z^2-1,
+// xz, x^2-y^2).
+__device__ __forceinline__ void sh_basis(const float d[3], float Y[9]) {
+  const float x = d[0], y = d[1], z = d[2];
+  Y[0] = 0.28209479177387814f;
+  Y[1] = 0.48860251190291992f * y;
+  Y[2] = 0.48860251190291992f * z;
+  Y[3] = 0.48860251190291992f * x;
+  Y[4] = 1.09254843059207907f * x * y;
+  Y[5] = 1.09254843059207907f * y * z;
+  Y[6] = 0.31539156525252005f * (3.f * z * z - 1.f);
+  Y[7] = 1.09254843059207907f * x * z;
+  Y[8] = 0.54627421529603959f * (x * x - y * y);
+}
+
+// Cell index and in-cell fraction of sample k along one axis from the
+// float-float position b + k*s. The fraction is accurate to ~1 ulp of 1.
+__device__ __forceinline__ void sample_axis(float bh, float bl, float sh, float sl,
+                                            float kf, int rm2, int& cell, float& frac) {
+  const float ph = kf * sh;
+  const float pe = fmaf(kf, sh, -ph);   // exact error of the product
+  const float s = bh + ph;              // two-sum
+  const float bb = s - bh;
+  const float e = (bh - (s - bb)) + (ph - bb);
+  const float corr = fmaf(kf, sl, e + bl + pe);
+  const float c = floorf(s);
+  float f = (s - c) + corr;
+  int ci = (int)c;
+  if (f < 0.f) { f += 1.f; ci -= 1; }
+  else if (f >= 1.f) { f -= 1.f; ci += 1; }
+  if (ci < 0) { f += (float)ci; ci = 0; }
+  else if (ci > rm2) { f += (float)(ci - rm2); ci = rm2; }
+  cell = ci;
+  frac = f;
+}
+
+// --------------------------------------------------------- record gathers
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ float f16_lo(uint32_t w) {
+  return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+}
+__device__ __forceinline__ float f16_hi(uint32_t w) {
+  return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+}
+
+// Loads the 28 values of record `link` into v[0..27] (density, then SH).
+template <int STORE>
+__device__ __forceinline__ void load_record(const void* rec, int32_t link, float v[28]) {
+  if constexpr (STORE == PLX_STORE_F32) {
+    const float4* p = reinterpret_cast<const float4*>(rec) + (int64_t)link * 8;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const float4 q = __ldg(p + j);
+      v[4 * j] = q.x; v[4 * j + 1] = q.y; v[4 * j + 2] = q.z; v[4 * j + 3] = q.w;
+    }
+  } else {
+    const uint4* p = reinterpret_cast<const uint4*>(rec) + (int64_t)link * 4;
+    uint32_t w[16];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 q = __ldg(p + j);
+      w[4 * j] = q.x; w[4 * j + 1] = q.y; w[4 * j + 2] = q.z; w[4 * j + 3] = q.w;
+    }
+    if constexpr (STORE == PLX_STORE_BF16) {
+#pragma unroll
+      for (int j = 0; j < 14; ++j) { v[2 * j] = bf16_lo(w[j]); v[2 * j + 1] = bf16_hi(w[j]); }
+    } else if constexpr (STORE == PLX_STORE_F16) {
+#pragma unroll
+      for (int j = 0; j < 14; ++j) { v[2 * j] = f16_lo(w[j]); v[2 * j + 1] = f16_hi(w[j]); }
+    } else {  // F32 density in slots 0-1, 27 BF16 SH in slots 2..28
+      v[0] = __uint_as_float(w[0]);
+#pragma unroll
+      for (int j = 0; j < 14; ++j) {
+        if (2 * j + 1 <= 27) v[2 * j + 1] = bf16_lo(w[j + 1]);
+        if (2 * j + 2 <= 27) v[2 * j + 2] = bf16_hi(w[j + 1]);
+      }
+    }
+  }
+}
+
+// Density and view-projected colour (per channel sum_k Y_k SH_k) of a corner.
+template <int STORE>
+__device__ __forceinline__ void load_corner(const void* rec, int32_t link, const float Y[9],
+                                            float& sig, float col[3]) {
+  float v[28];
+  load_record<STORE>(rec, link, v);
+  sig = v[0];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a = fmaf(Y[k], v[1 + 9 * ch + k], a);
+    col[ch] = a;
+  }
+}
+
+// The 8 links of cell (ix, iy, iz); corner c = dx + 2 dy + 4 dz.
+__device__ __forceinline__ void load_links(const GridView& g, int ix, int iy, int iz,
+                                           int32_t l[8]) {
+  const int64_t sx = 1, sy = g.rx, sz = (int64_t)g.rx * g.ry;
+  const int32_t* p = g.links + (int64_t)iz * sz + (int64_t)iy * sy + ix;
+  l[0] = __ldg(p);
+  l[1] = __ldg(p + sx);
+  l[2] = __ldg(p + sy);
+  l[3] = __ldg(p + sy + sx);
+  l[4] = __ldg(p + sz);
+  l[5] = __ldg(p + sz + sx);
+  l[6] = __ldg(p + sz + sy);
+  l[7] = __ldg(p + sz + sy + sx);
+}
+
+// Loads the cell's corner cache; returns true if no corner is allocated.
+template <int STORE>
+__device__ __forceinline__ bool load_cell(const GridView& g, int ix, int iy, int iz,
+                                          const float Y[9], int32_t l[8], float cs[8],
+                                          float cc[8][3]) {
+  load_links(g, ix, iy, iz, l);
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (l[c] >= 0) {
+      any = true;
+      load_corner<STORE>(g.rec, l[c], Y, cs[c], cc[c]);
+    } else {
+      cs[c] = 0.f;
+      cc[c][0] = cc[c][1] = cc[c][2] = 0.f;
+    }
+  }
+  return !any;
+}
+
+__device__ __forceinline__ void corner_weights(float fx, float fy, float fz, float w[8]) {
+  const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
+  const float a0 = gy * gz, a1 = fy * gz, a2 = gy * fz, a3 = fy * fz;
+  w[0] = gx * a0; w[1] = fx * a0;
+  w[2] = gx * a1; w[3] = fx * a1;
+  w[4] = gx * a2; w[5] = fx * a2;
+  w[6] = gx * a3; w[7] = fx * a3;
+}
+
+__device__ __forceinline__ float activate(float chat, int act, float& dact) {
+  if (act == PLX_ACT_IDENTITY) { dact = 1.f; return chat; }
+  const float c = 1.f / (1.f + __expf(-chat));
+  dact = c * (1.f - c);
+  return c;
+}
+
+// 1 - exp(-x) for x >= 0 without cancellation, and exp(-x).
+__device__ __forceinline__ void alpha_of(float x, float& alpha, float& keep) {
+  keep = expf(-x);
+  alpha = -expm1f(-x);
+}
+
+__device__ __forceinline__ bool depth_valid(float d) { return isfinite(d) && d > 0.f; }
+
+}  // namespace plx

@@ -1,0 +1,311 @@
+"""ctypes binding of ``libplx.so`` (C ABI in ``include/plx.h``).
+
+Argument marshalling only: every step of the render, its adjoints and the pose
+step runs in the library's CUDA kernels. PyTorch provides device memory and
+the current stream. Importing this module loads the library and raises if it
+is missing: there is no CPU fallback.
+
+Function names follow the C ABI (``grid_create`` -> ``plx_grid_create`` ...).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libplx.so")
+
+STORE_F32, STORE_BF16, STORE_F16, STORE_F32_BF16 = 0, 1, 2, 3
+STORAGE = {"f32": STORE_F32, "bf16": STORE_BF16, "f16": STORE_F16, "f32_bf16": STORE_F32_BF16}
+ACT_SIGMOID, ACT_IDENTITY = 0, 1
+MAX_CAMERAS = 128
+GRAD_STRIDE = 32
+
+STATUS = {0: "PLX_OK", 1: "PLX_EINVAL", 2: "PLX_ENOMEM", 3: "PLX_ECUDA",
+          4: "PLX_EDEVICE_CHECK", 5: "PLX_ETIMEOUT", 6: "PLX_EUNSUPPORTED"}
+
+
+class PlxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("res", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("n_alloc", C.c_int64), ("storage", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class Cameras(C.Structure):
+    _fields_ = [("n_cams", C.c_int32), ("reserved", C.c_int32),
+                ("intr", C.POINTER(Intrinsics)), ("poses", C.c_void_p)]
+
+
+class Rays(C.Structure):
+    _fields_ = [("n_rays", C.c_int64), ("cam_id", C.c_void_p), ("pixel", C.c_void_p)]
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("step", C.c_double), ("near_t", C.c_double), ("stop_T", C.c_double),
+                ("bg", C.c_float * 3), ("lambda_d", C.c_float), ("max_samples", C.c_int32),
+                ("color_act", C.c_int32), ("depth_is_z", C.c_int32), ("reserved", C.c_int32)]
+
+
+SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload",
+           "plx_grid_download", "plx_grid_info", "plx_grid_destroy", "plx_render_forward",
+           "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
+           "plx_grid_check"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2307_03404_b300.build` (there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.plx_last_error.restype = C.c_char_p
+    lib.plx_version.restype = C.c_char_p
+    sig = {
+        "plx_grid_create": [C.POINTER(GridDesc), P, P, P, P, C.POINTER(P)],
+        "plx_grid_upload": [P, P, P, P],
+        "plx_grid_download": [P, P, P, P],
+        "plx_grid_info": [P, C.POINTER(GridDesc)],
+        "plx_grid_destroy": [P],
+        "plx_grid_check": [P, P],
+        "plx_render_forward": [P, C.POINTER(Cameras), C.POINTER(Rays), C.POINTER(RenderOpts),
+                               P, P, P, P, P],
+        "plx_render_backward_grid": [P, C.POINTER(Cameras), C.POINTER(Rays),
+                                     C.POINTER(RenderOpts), P, P, P, P, P, P, P],
+        "plx_render_backward_pose": [P, C.POINTER(Cameras), I32, C.POINTER(Rays),
+                                     C.POINTER(RenderOpts), P, P, P, P, P, P],
+        "plx_pose_step": [P, P, D, P, P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status):
+    if status != 0:
+        raise PlxError(status, _lib.plx_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def version() -> str:
+    return _lib.plx_version().decode()
+
+
+# ----------------------------------------------------------------- grid
+class Grid:
+    """Library-owned copy of a sparse grid (``plx_grid``)."""
+
+    def __init__(self, res, lo, hi, links, density, sh, storage="f32", stream=None):
+        dev = torch.device("cuda")
+        links = torch.as_tensor(links).to(dev, torch.int32).contiguous()
+        density = torch.as_tensor(density).to(dev, torch.float32).contiguous()
+        sh = torch.as_tensor(sh).to(dev, torch.float32).reshape(-1, 27).contiguous()
+        d = GridDesc()
+        d.res[:] = [int(v) for v in res]
+        d.lo[:] = [float(v) for v in lo]
+        d.hi[:] = [float(v) for v in hi]
+        d.n_alloc = int(density.shape[0])
+        d.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        h = C.c_void_p()
+        _check(_lib.plx_grid_create(C.byref(d), _ptr(links), _ptr(density), _ptr(sh),
+                                    _stream(stream), C.byref(h)))
+        self._h = h
+        self.desc = d
+        self.n_alloc = int(d.n_alloc)
+        self.storage = d.storage
+        self.res = tuple(int(v) for v in res)
+        self.lo = np.array(lo, np.float64)
+        self.hi = np.array(hi, np.float64)
+
+    @classmethod
+    def from_scene(cls, grid, storage="f32"):
+        return cls(grid.res, grid.lo, grid.hi, torch.from_numpy(grid.links),
+                   torch.from_numpy(np.ascontiguousarray(grid.density, np.float32)),
+                   torch.from_numpy(np.ascontiguousarray(grid.sh, np.float32)), storage)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def upload(self, density, sh, stream=None):
+        _check(_lib.plx_grid_upload(self._h, _ptr(density.contiguous()),
+                                    _ptr(sh.contiguous()), _stream(stream)))
+
+    def download(self, stream=None):
+        density = torch.empty(self.n_alloc, device="cuda")
+        sh = torch.empty(self.n_alloc, 27, device="cuda")
+        _check(_lib.plx_grid_download(self._h, _ptr(density), _ptr(sh), _stream(stream)))
+        return density, sh
+
+    def check(self, stream=None):
+        _check(_lib.plx_grid_check(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(_lib.plx_grid_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# -------------------------------------------------------------- cameras
+class CameraSet:
+    """Intrinsics on the host, poses [n, 12] float64 on the device."""
+
+    def __init__(self, cams: Sequence, poses: torch.Tensor | None = None):
+        cams = list(cams)
+        if not 1 <= len(cams) <= MAX_CAMERAS:
+            raise ValueError(f"1..{MAX_CAMERAS} cameras")
+        self._intr = (Intrinsics * len(cams))()
+        for i, c in enumerate(cams):
+            self._intr[i].fx, self._intr[i].fy = float(c.fx), float(c.fy)
+            self._intr[i].cx, self._intr[i].cy = float(c.cx), float(c.cy)
+            self._intr[i].width, self._intr[i].height = int(c.width), int(c.height)
+        if poses is None:
+            poses = torch.tensor(np.stack([np.asarray(c.T_wc, np.float64).reshape(12)
+                                           for c in cams]), dtype=torch.float64, device="cuda")
+        self.poses = poses.contiguous()
+        self.sizes = [(int(c.width), int(c.height)) for c in cams]
+        self.n = len(cams)
+
+    def struct(self):
+        s = Cameras()
+        s.n_cams = self.n
+        s.intr = C.cast(self._intr, C.POINTER(Intrinsics))
+        s.poses = self.poses.data_ptr()
+        return s
+
+    def n_pixels(self, cam=None):
+        if cam is not None:
+            w, h = self.sizes[cam]
+            return w * h
+        return sum(w * h for w, h in self.sizes)
+
+
+def make_rays(cam_id=None, pixel=None):
+    """Rays struct plus the tensors it points to (None = dense mode). An empty
+    list is passed with non-null placeholder pointers: null means dense."""
+    r = Rays()
+    keep = []
+    if pixel is None:
+        r.n_rays = 0
+        return r, keep
+    pixel = torch.as_tensor(pixel).to("cuda", torch.int32).contiguous()
+    r.n_rays = int(pixel.shape[0])
+    if cam_id is not None:
+        cam_id = torch.as_tensor(cam_id).to("cuda", torch.int32).contiguous()
+    if r.n_rays == 0:
+        pixel = torch.zeros(1, dtype=torch.int32, device="cuda")
+        cam_id = None if cam_id is None else torch.zeros(1, dtype=torch.int32, device="cuda")
+    keep.append(pixel)
+    r.pixel = pixel.data_ptr()
+    if cam_id is not None:
+        keep.append(cam_id)
+        r.cam_id = cam_id.data_ptr()
+    return r, keep
+
+
+def make_opts(step, near=0.0, stop_T=0.0, bg=(0.0, 0.0, 0.0), lambda_d=1.0,
+              max_samples=1 << 30, color_act="sigmoid", depth_is_z=True):
+    o = RenderOpts()
+    o.step, o.near_t, o.stop_T = float(step), float(near), float(stop_T)
+    o.bg[:] = [float(v) for v in bg]
+    o.lambda_d = float(lambda_d)
+    o.max_samples = int(min(max_samples, 2 ** 31 - 1))
+    o.color_act = {"sigmoid": ACT_SIGMOID, "identity": ACT_IDENTITY}[color_act]
+    o.depth_is_z = int(bool(depth_is_z))
+    return o
+
+
+def opts_from_dict(d):
+    return make_opts(d["step"], d.get("near", 0.0), d.get("stop_T", 0.0), d.get("bg", (0, 0, 0)),
+                     d.get("lambda_d", 1.0), d.get("max_samples", 1 << 30),
+                     d.get("color_act", "sigmoid"), d.get("depth_is_z", True))
+
+
+# ----------------------------------------------------------- entry points
+def render_forward(grid: Grid, cams: CameraSet, opts, rays=None, state=True, counts=False,
+                   out=None, stream=None):
+    """plx_render_forward. ``rays`` = (cam_id, pixel) or None (dense).
+    Returns dict(rgb [n,3], depth [n], state [n] | None, counts [n,2] | None)."""
+    r, keep = make_rays(*(rays if rays is not None else (None, None)))
+    n = r.n_rays if rays is not None else cams.n_pixels()
+    if out is None:
+        out = {"rgb": torch.empty(n, 3, device="cuda"), "depth": torch.empty(n, device="cuda"),
+               "state": torch.empty(n, device="cuda") if state else None,
+               "counts": torch.empty(n, 2, device="cuda", dtype=torch.int32) if counts else None}
+    cs = cams.struct()
+    _check(_lib.plx_render_forward(grid.handle, C.byref(cs), C.byref(r), C.byref(opts),
+                                   _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out.get("state")),
+                                   _ptr(out.get("counts")), _stream(stream)))
+    return out
+
+
+def render_backward_grid(grid: Grid, cams: CameraSet, opts, rgb_target, depth_target, rgb,
+                         depth, rays=None, grad=None, loss=None, stream=None):
+    """plx_render_backward_grid. Adds into ``grad`` [n_alloc, 32] (allocated
+    zeroed when None); returns (grad, loss [2] float64 = (L, M))."""
+    r, keep = make_rays(*(rays if rays is not None else (None, None)))
+    if grad is None:
+        grad = torch.zeros(grid.n_alloc, GRAD_STRIDE, device="cuda")
+    if loss is None:
+        loss = torch.empty(2, device="cuda", dtype=torch.float64)
+    cs = cams.struct()
+    _check(_lib.plx_render_backward_grid(grid.handle, C.byref(cs), C.byref(r), C.byref(opts),
+                                         _ptr(rgb_target), _ptr(depth_target), _ptr(rgb),
+                                         _ptr(depth), _ptr(grad), _ptr(loss), _stream(stream)))
+    return grad, loss
+
+
+def render_backward_pose(grid: Grid, cams: CameraSet, cam: int, opts, rgb_target, depth_target,
+                         rays=None, out=None, stream=None):
+    """plx_render_backward_pose for camera ``cam``; ``rays`` = pixel list or None.
+    Returns (JtWJ [6,6], JtWr [6], loss [2]) float64 device tensors."""
+    r, keep = make_rays(None, rays)
+    if out is None:
+        out = (torch.empty(6, 6, device="cuda", dtype=torch.float64),
+               torch.empty(6, device="cuda", dtype=torch.float64),
+               torch.empty(2, device="cuda", dtype=torch.float64))
+    cs = cams.struct()
+    _check(_lib.plx_render_backward_pose(grid.handle, C.byref(cs), int(cam), C.byref(r),
+                                         C.byref(opts), _ptr(rgb_target), _ptr(depth_target),
+                                         _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
+                                         _stream(stream)))
+    return out
+
+
+def pose_step(JtWJ, JtWr, pose, damping=0.0, xi_out=None, status=None, stream=None):
+    """plx_pose_step: pose (device float64 [12] view) <- exp(xi^) pose."""
+    _check(_lib.plx_pose_step(_ptr(JtWJ), _ptr(JtWr), float(damping), _ptr(pose), _ptr(xi_out),
+                              _ptr(status), _stream(stream)))

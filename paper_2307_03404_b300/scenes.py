@@ -219,9 +219,24 @@ def _prim_sdf(P, prim):
     return _box_sdf(P, prim["c"], prim["half"])
 
 
-def _prim_bounds(prim):
-    ext = prim["r"] if prim["kind"] == "sphere" else np.max(prim["half"])
-    return prim["c"] - ext * np.sqrt(3.0), prim["c"] + ext * np.sqrt(3.0)
+def _prim_sdf_sep(xs, ys, zs, prim):
+    """Same distance as _prim_sdf on the grid zs x ys x xs, from 1-D axes."""
+    c = prim["c"].astype(np.float32)
+    if prim["kind"] == "sphere":
+        d2 = ((zs - c[2]) ** 2)[:, None, None] + ((ys - c[1]) ** 2)[None, :, None] \
+            + ((xs - c[0]) ** 2)[None, None, :]
+        return np.sqrt(d2) - np.float32(prim["r"])
+    hf = prim["half"].astype(np.float32)
+    qx, qy, qz = np.abs(xs - c[0]) - hf[0], np.abs(ys - c[1]) - hf[1], np.abs(zs - c[2]) - hf[2]
+    out2 = (np.maximum(qz, 0) ** 2)[:, None, None] + (np.maximum(qy, 0) ** 2)[None, :, None] \
+        + (np.maximum(qx, 0) ** 2)[None, None, :]
+    inside = np.minimum(np.maximum(np.maximum(qz[:, None, None], qy[None, :, None]),
+                                   qx[None, None, :]), 0)
+    return np.sqrt(out2) + inside
+
+
+def _prim_extent(prim):
+    return np.full(3, prim["r"]) if prim["kind"] == "sphere" else prim["half"]
 
 
 def _random_prims(rng, room_lo, room_hi, n):
@@ -241,38 +256,38 @@ def _random_prims(rng, room_lo, room_hi, n):
     return prims
 
 
-def _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims, dtype=np.float32):
-    """Signed distance (positive in free space) at every vertex, built slab by
-    slab over z; walls are the faces of the room box, solid outside it."""
-    xs = np.linspace(lo[0], hi[0], R).astype(dtype)
-    ys = np.linspace(lo[1], hi[1], R).astype(dtype)
-    zs = np.linspace(lo[2], hi[2], R).astype(dtype)
-    wx = np.minimum(xs - room_lo[0], room_hi[0] - xs).astype(dtype)
-    wy = np.minimum(ys - room_lo[1], room_hi[1] - ys).astype(dtype)
-    wz = np.minimum(zs - room_lo[2], room_hi[2] - zs).astype(dtype)
-    s = np.empty((R, R, R), dtype)
+def _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims, margin_vox=12):
+    """Signed distance (positive in free space) at every vertex: walls are the
+    faces of the room box (solid outside it). Each primitive is evaluated only
+    within ``margin_vox`` voxels of its extent; farther away its distance
+    exceeds any band width used here, so the band is unchanged."""
+    xs = np.linspace(lo[0], hi[0], R).astype(np.float32)
+    ys = np.linspace(lo[1], hi[1], R).astype(np.float32)
+    zs = np.linspace(lo[2], hi[2], R).astype(np.float32)
+    wx = np.minimum(xs - room_lo[0], room_hi[0] - xs).astype(np.float32)
+    wy = np.minimum(ys - room_lo[1], room_hi[1] - ys).astype(np.float32)
+    wz = np.minimum(zs - room_lo[2], room_hi[2] - zs).astype(np.float32)
+    s = np.empty((R, R, R), np.float32)
     np.minimum(wz[:, None, None], wy[None, :, None], out=s)
     np.minimum(s, wx[None, None, :], out=s)
     h = (hi - lo) / (R - 1)
     for p in prims:
-        blo, bhi = _prim_bounds(p)
-        i0 = np.clip(np.floor((blo - lo) / h).astype(int) - 3, 0, R - 1)
-        i1 = np.clip(np.ceil((bhi - lo) / h).astype(int) + 4, 0, R)
+        ext = _prim_extent(p) + margin_vox * h
+        i0 = np.clip(np.floor((p["c"] - ext - lo) / h).astype(int), 0, R - 1)
+        i1 = np.clip(np.ceil((p["c"] + ext - lo) / h).astype(int) + 1, 0, R)
         sub = s[i0[2]:i1[2], i0[1]:i1[1], i0[0]:i1[0]]
-        Zs, Ys, Xs = np.meshgrid(zs[i0[2]:i1[2]], ys[i0[1]:i1[1]], xs[i0[0]:i1[0]],
-                                 indexing="ij")
-        P = np.stack([Xs, Ys, Zs], axis=-1).astype(np.float64)
-        np.minimum(sub, _prim_sdf(P, p).astype(dtype), out=sub)
+        np.minimum(sub, _prim_sdf_sep(xs[i0[0]:i1[0]], ys[i0[1]:i1[1]], zs[i0[2]:i1[2]], p),
+                   out=sub)
     return s
 
 
 def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 3.2,
                wall_inset_vox: float = 4.0, border: int = 2) -> Scene:
     """Analytic room: the six faces of a box inset by ``wall_inset_vox`` voxels
-    from the grid box, plus ``n_prims`` random spheres and boxes. Vertices
-    within a band around the surfaces are allocated; the band width is the
-    quantile of |sdf| that allocates the fraction ``occupancy`` of all
-    vertices. The ``border`` outermost vertex layers are never allocated.
+    from the grid box, plus ``n_prims`` random spheres and boxes. The vertices
+    closest to the surfaces are allocated, as many as the fraction
+    ``occupancy`` of all vertices (distance ties broken by a seeded jitter of
+    +-0.05 voxel); the ``border`` outermost vertex layers are never allocated.
     Allocated density rises across the band into the solid, about 0.6 / h at
     the inner band edge and slightly negative at the outer one; SH ~ N(0, 0.3).
     """
@@ -280,28 +295,32 @@ def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 
     lo = np.full(3, -half)
     hi = np.full(3, half)
     h = (hi - lo) / (R - 1)
+    hm = float(h.min())
     room_lo = lo + wall_inset_vox * h
     room_hi = hi - wall_inset_vox * h
     prims = _random_prims(rng, room_lo, room_hi, n_prims)
     s = _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims)
     b = border
-    inner = np.zeros(R, bool)
-    inner[b:R - b] = True
-    st = max(1, R // 128)
-    sample = np.abs(s[::st, ::st, ::st]).reshape(-1)
-    w = float(np.quantile(sample, occupancy))
-    alloc = np.abs(s) <= w
-    alloc &= inner[:, None, None] & inner[None, :, None] & inner[None, None, :]
-    n = int(alloc.sum())
-    links = np.full((R, R, R), -1, np.int32)
-    links[alloc] = np.arange(n, dtype=np.int32)
-    sv = s[alloc].astype(np.float64)
-    hm = float(h.min())
+    key = np.abs(s)
+    key += (rng.random(key.shape, dtype=np.float32) - np.float32(0.5)) * np.float32(0.1 * hm)
+    key[:b], key[R - b:] = np.inf, np.inf
+    key[:, :b], key[:, R - b:] = np.inf, np.inf
+    key[:, :, :b], key[:, :, R - b:] = np.inf, np.inf
+    n = int(round(occupancy * R ** 3))
+    flat = key.reshape(-1)
+    sel = np.argpartition(flat, n - 1)[:n] if n > 0 else np.zeros(0, np.int64)
+    sel.sort()
+    del key, flat
+    links = np.full(R ** 3, -1, np.int32)
+    links[sel] = np.arange(n, dtype=np.int32)
+    links = links.reshape(R, R, R)
+    sv = s.reshape(-1)[sel].astype(np.float64)
+    del s
+    w = max(float(np.abs(sv).max()), hm)
     density = ((0.6 / hm) * (0.5 - 0.6 * sv / w)
                + (0.05 / hm) * rng.standard_normal(n)).astype(np.float32)
     sh = rng.standard_normal((n, N_SH), dtype=np.float32)
     sh *= np.float32(0.3)
-    del s
     grid = Grid((R, R, R), lo, hi, links, density, sh)
     return Scene(grid, prims, room_lo, room_hi)
 

@@ -1,0 +1,112 @@
+"""Host-side checks of the C ABI that need no GPU.
+
+The CUDA library is linked against a static CUDA runtime, so it loads on a
+machine without a GPU; these tests only make calls that fail argument
+validation before any CUDA call.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "plx.h")
+LIB = os.path.join(ROOT, "paper_2307_03404_b300", "libplx.so")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2307_03404_b300 import build
+
+    build.build()
+    return C.CDLL(LIB)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(plx_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["plx_grid_create", "plx_render_forward", "plx_render_backward_grid",
+                     "plx_render_backward_pose", "plx_pose_step", "plx_grid_destroy",
+                     "plx_grid_upload", "plx_grid_download", "plx_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (plx_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_uses_the_declared_names():
+    from paper_2307_03404_b300 import plx
+
+    assert set(plx.SYMBOLS) == set(declared_functions())
+    assert plx.version().startswith("plx")
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """Compile a probe against plx.h with gcc and compare sizes and offsets."""
+    from paper_2307_03404_b300 import plx
+
+    src = tmp_path / "probe.c"
+    src.write_text(r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "plx.h"
+#define P(T, F) printf(#T "." #F " %zu\n", offsetof(T, F))
+#define S(T) printf(#T " %zu\n", sizeof(T))
+int main(void) {
+  S(plx_grid_desc); P(plx_grid_desc, lo); P(plx_grid_desc, hi); P(plx_grid_desc, n_alloc);
+  P(plx_grid_desc, storage);
+  S(plx_intrinsics); P(plx_intrinsics, width);
+  S(plx_cameras); P(plx_cameras, intr); P(plx_cameras, poses);
+  S(plx_rays); P(plx_rays, cam_id); P(plx_rays, pixel);
+  S(plx_render_opts); P(plx_render_opts, bg); P(plx_render_opts, lambda_d);
+  P(plx_render_opts, max_samples); P(plx_render_opts, depth_is_z);
+  return 0;
+}
+""")
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    m = {"plx_grid_desc": plx.GridDesc, "plx_intrinsics": plx.Intrinsics,
+         "plx_cameras": plx.Cameras, "plx_rays": plx.Rays, "plx_render_opts": plx.RenderOpts}
+    for key, val in got.items():
+        if "." in key:
+            t, f = key.split(".")
+            assert getattr(m[t], f).offset == int(val), key
+        else:
+            assert C.sizeof(m[key]) == int(val), key
+
+
+def test_argument_errors_are_reported_without_touching_the_gpu(lib):
+    from paper_2307_03404_b300 import plx
+
+    lib = plx._lib
+    h = C.c_void_p()
+    assert lib.plx_grid_create(None, None, None, None, None, C.byref(h)) == 1
+    assert b"null" in lib.plx_last_error()
+    d = plx.GridDesc()
+    d.res[:] = [1, 4, 4]
+    d.hi[:] = [1, 1, 1]
+    assert lib.plx_grid_create(C.byref(d), None, None, None, None, C.byref(h)) == 1
+    assert b"res[0]" in lib.plx_last_error()
+    d.res[:] = [4, 4, 4]
+    d.storage = 9
+    assert lib.plx_grid_create(C.byref(d), None, None, None, None, C.byref(h)) == 1
+    assert b"storage" in lib.plx_last_error()
+    assert lib.plx_pose_step(None, None, 0.0, None, None, None, None) == 1
+    x = (C.c_double * 40)()
+    assert lib.plx_pose_step(x, x, -1.0, x, None, None, None) == 1
+    assert b"damping" in lib.plx_last_error()
+    assert lib.plx_render_forward(None, None, None, None, None, None, None, None, None) == 1
+    assert lib.plx_grid_destroy(None) == 0
