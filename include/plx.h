@@ -217,6 +217,40 @@ plx_status plx_render_backward_pose(const plx_grid *grid,
                                     const float *depth_target, double *JtWJ,
                                     double *JtWr, double *loss, void *stream);
 
+/* Allocation-free variant of plx_render_backward_pose. The paper has no
+ * counterpart. It serves callers that cannot allocate device memory while
+ * they run, so cannot call plx_grid_create: a tracking loop under a real-time
+ * budget that forbids allocation after start-up, or an application whose
+ * device memory all belongs to another allocator (a pool this library cannot
+ * see). The caller passes the grid as plain arrays instead of a handle:
+ *   desc    HOST descriptor (res, lo, hi, n_alloc, storage)
+ *   links   DEVICE int32 [res_z][res_y][res_x]; each entry -1 or in
+ *           [0, n_alloc). NOT checked here (plx_grid_create checks them).
+ *   records DEVICE, 16-byte aligned, one record per allocated vertex in the
+ *           layout of desc->storage: PLX_STORE_F32 = 32 floats (slot 0
+ *           density, slots 1..27 SH in canonical order, 28..31 ignored);
+ *           PLX_STORE_BF16 / PLX_STORE_F16 = 32 16-bit values in the same
+ *           slots; PLX_STORE_F32_BF16 = 64 bytes, density as float in bytes
+ *           0..3, the 27 SH as bfloat16 from byte 4.
+ * Every other argument and all outputs are those of plx_render_backward_pose.
+ * Scratch: a static device array inside the library holding the FP64 partial
+ * sums of at most 1024 thread blocks (about 256 KiB), kept by every GPU that
+ * loads the library until the process exits. The kernel strides over ray
+ * tiles with at most that many blocks, so every ray count fits; a device
+ * index of 64 or more is rejected with PLX_EUNSUPPORTED. The first call on a
+ * device looks up the array's device address with that device current: make
+ * that first call before any stream capture. All calls share the array, and
+ * each call clears its counters on its own stream first: calls that overlap
+ * on the GPU (several streams or host threads) race and return wrong sums.
+ * Pixel-list entries out of range are skipped and do not count in M. Nothing
+ * is allocated or freed. */
+plx_status plx_render_backward_pose_noalloc(
+    const plx_grid_desc *desc, const int32_t *links, const void *records,
+    const plx_cameras *cams, int32_t cam, const plx_rays *rays,
+    const plx_render_opts *opts, const float *rgb_target,
+    const float *depth_target, double *JtWJ, double *JtWr, double *loss,
+    void *stream);
+
 /* Sec. 5.3 (the pose is optimised directly). Gauss-Newton step, on the
  * device in FP64: solves (JtWJ + damping I) xi = -JtWr by Cholesky and sets
  * pose <- exp(xi^) pose (SE(3) exponential: Rodrigues rotation, V rho

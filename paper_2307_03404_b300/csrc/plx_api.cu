@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "plx_internal.cuh"
@@ -425,3 +426,99 @@ plx_status plx_pose_step(const double* JtWJ, const double* JtWr, double damping,
 }
 
 }  // extern "C"
+
+// -------------------------------------------------- allocation-free variant
+// plx_render_backward_pose_noalloc keeps its scratch (error word, retirement
+// counter and the FP64 per-block partial sums) in this file-scope array
+// instead of memory that plx_grid_create allocated. Every GPU that loads the
+// library holds the array until the process exits. Host code must not pass
+// the array's name to a kernel: its device address comes from
+// cudaGetSymbolAddress, taken once per device.
+#define PLX_NOALLOC_MAX_BLOCKS 1024
+#define PLX_NOALLOC_MAX_DEVICES 64
+static __device__ __align__(256) unsigned char
+    g_noalloc_scratch[sizeof(Workspace) + PLX_NOALLOC_MAX_BLOCKS * 32 * sizeof(double)];
+
+static std::mutex g_noalloc_mu;
+static char* g_noalloc_ptr[PLX_NOALLOC_MAX_DEVICES];
+static int g_noalloc_blocks[PLX_NOALLOC_MAX_DEVICES][4];
+
+// Device address of the scratch and the block cap per storage mode, set up on
+// the first call on each device (with that device current).
+static plx_status noalloc_setup(int dev, int storage, char** ptr, int* max_blocks) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(PLX_ECUDA, "render_backward_pose_noalloc: cudaGetSymbolAddress: %s",
+                  cudaGetErrorString(e));
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+      return fail(PLX_ECUDA, "render_backward_pose_noalloc: %s", cudaGetErrorString(e));
+    for (int st = 0; st < 4; ++st) {
+      const int b = sms * pose_kernel_blocks_per_sm(st);
+      g_noalloc_blocks[dev][st] = b < PLX_NOALLOC_MAX_BLOCKS ? b : PLX_NOALLOC_MAX_BLOCKS;
+    }
+    g_noalloc_ptr[dev] = static_cast<char*>(p);
+  }
+  *ptr = g_noalloc_ptr[dev];
+  *max_blocks = g_noalloc_blocks[dev][storage];
+  return PLX_OK;
+}
+
+extern "C" plx_status plx_render_backward_pose_noalloc(
+    const plx_grid_desc* desc, const int32_t* links, const void* records,
+    const plx_cameras* cams, int32_t cam, const plx_rays* rays, const plx_render_opts* opts,
+    const float* rgb_target, const float* depth_target, double* JtWJ, double* JtWr,
+    double* loss, void* stream) {
+  const char* what = "render_backward_pose_noalloc";
+  if (!desc) return fail(PLX_EINVAL, "%s: null desc", what);
+  for (int a = 0; a < 3; ++a) {
+    if (desc->res[a] < 2 || desc->res[a] > 65536)
+      return fail(PLX_EINVAL, "%s: res[%d] = %d out of [2, 65536]", what, a, desc->res[a]);
+    if (!(desc->hi[a] > desc->lo[a]) || !std::isfinite(desc->lo[a]) || !std::isfinite(desc->hi[a]))
+      return fail(PLX_EINVAL, "%s: need lo < hi on axis %d", what, a);
+  }
+  if (desc->n_alloc < 0 || desc->n_alloc > INT32_MAX)
+    return fail(PLX_EINVAL, "%s: n_alloc %lld out of range", what, (long long)desc->n_alloc);
+  if (desc->storage < PLX_STORE_F32 || desc->storage > PLX_STORE_F32_BF16)
+    return fail(PLX_EINVAL, "%s: unknown storage %d", what, desc->storage);
+  if (!links || (desc->n_alloc > 0 && !records))
+    return fail(PLX_EINVAL, "%s: null links or records", what);
+  if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
+    return fail(PLX_EINVAL, "%s: records must be 16-byte aligned", what);
+  if (cam < 0) return fail(PLX_EINVAL, "%s: cam < 0", what);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PLX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  if (dev < 0 || dev >= PLX_NOALLOC_MAX_DEVICES)
+    return fail(PLX_EUNSUPPORTED, "%s: device %d beyond %d", what, dev, PLX_NOALLOC_MAX_DEVICES);
+  char* scratch = nullptr;
+  int max_blocks = 0;
+  plx_status st = noalloc_setup(dev, desc->storage, &scratch, &max_blocks);
+  if (st != PLX_OK) return st;
+  // a grid view on the caller's arrays; nothing is allocated or copied
+  plx_grid view;
+  view.desc = *desc;
+  view.links = const_cast<int32_t*>(links);
+  view.rec = const_cast<void*>(records);
+  view.rec_bytes = record_bytes(desc->storage);
+  view.ws = scratch;
+  for (int a = 0; a < 3; ++a) view.inv_h[a] = (double)(desc->res[a] - 1) / (desc->hi[a] - desc->lo[a]);
+  Common P;
+  st = build_common(what, &view, cams, rays, opts, cam, P);
+  if (st != PLX_OK) return st;
+  if (!JtWJ || !JtWr || !loss) return fail(PLX_EINVAL, "%s: null output", what);
+  if (P.ct.n_rays > 0 && (!rgb_target || !depth_target))
+    return fail(PLX_EINVAL, "%s: null target", what);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* ws = reinterpret_cast<Workspace*>(scratch);
+  e = cudaMemsetAsync(ws, 0, sizeof(Workspace), s);  // error word and retirement counter
+  if (e != cudaSuccess) return fail(PLX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  launch_backward_pose(desc->storage, P, rgb_target, depth_target,
+                       reinterpret_cast<double*>(scratch + sizeof(Workspace)), &ws->retire, JtWJ,
+                       JtWr, loss, max_blocks, s);
+  return launch_check(what);
+}

@@ -64,7 +64,7 @@ class RenderOpts(C.Structure):
 SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload",
            "plx_grid_download", "plx_grid_info", "plx_grid_destroy", "plx_render_forward",
            "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
-           "plx_grid_check"]
+           "plx_grid_check", "plx_render_backward_pose_noalloc"]
 
 
 def _load():
@@ -89,6 +89,9 @@ def _load():
         "plx_render_backward_pose": [P, C.POINTER(Cameras), I32, C.POINTER(Rays),
                                      C.POINTER(RenderOpts), P, P, P, P, P, P],
         "plx_pose_step": [P, P, D, P, P, P, P],
+        "plx_render_backward_pose_noalloc": [C.POINTER(GridDesc), P, P, C.POINTER(Cameras), I32,
+                                             C.POINTER(Rays), C.POINTER(RenderOpts), P, P, P, P,
+                                             P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
