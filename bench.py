@@ -301,6 +301,7 @@ def run_ours(args):
                         "ms_per_step": t_other / K,
                         "step_frac": (fo_b + bo_b) / (hbm * 1e9) * 1e3 / (t_other / K)},
         "loss": main["loss"],
+        "kernels_ms": {"forward": fwd_ms, "backward_grid": bwd_ms},
     }
     if not args.no_tracking:
         line["tracking"] = run_tracking(args, world, rank, barrier)

@@ -40,6 +40,8 @@ struct plx_grid {
   plx_grid_desc desc;
   int32_t* links = nullptr;
   void* rec = nullptr;
+  uint8_t* blk = nullptr;         // empty-space blocks (null: none)
+  int nb[3] = {0, 0, 0};
   int rec_bytes = 0;
   char* ws = nullptr;
   int max_pose_blocks = 0;
@@ -145,6 +147,25 @@ __global__ void k_check_links(const int32_t* __restrict__ links, int64_t n, int6
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 2);
 }
 
+// Marks every 8^3-cell block that has a cell with an allocated corner: vertex
+// x is a corner of cells x-1 and x (those that exist), on each axis.
+__global__ void k_build_blocks(const int32_t* __restrict__ links, int rx, int ry, int rz,
+                               uint8_t* __restrict__ blk, int nbx, int nby) {
+  const int64_t n = (int64_t)rx * ry * rz;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (links[i] < 0) continue;
+    const int x = (int)(i % rx), y = (int)((i / rx) % ry), z = (int)(i / ((int64_t)rx * ry));
+    const int x0 = x > 0 ? x - 1 : x, x1 = x < rx - 1 ? x : x - 1;
+    const int y0 = y > 0 ? y - 1 : y, y1 = y < ry - 1 ? y : y - 1;
+    const int z0 = z > 0 ? z - 1 : z, z1 = z < rz - 1 ? z : z - 1;
+    for (int cz = z0; cz <= z1; ++cz)
+      for (int cy = y0; cy <= y1; ++cy)
+        for (int cx = x0; cx <= x1; ++cx)
+          blk[((int64_t)(cz >> kBlkShift) * nby + (cy >> kBlkShift)) * nbx + (cx >> kBlkShift)] = 1;
+  }
+}
+
 static unsigned grid_stride_blocks(int64_t n, int num_sms) {
   const int64_t want = (n + 255) / 256;
   const int64_t cap = (int64_t)num_sms * 8;
@@ -185,6 +206,7 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
   auto cleanup = [&](plx_status st) {
     cudaFree(g->links);
     cudaFree(g->rec);
+    cudaFree(g->blk);
     cudaFree(g->ws);
     delete g;
     return st;
@@ -202,16 +224,22 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
   e = cudaMalloc(&g->links, (size_t)n_links * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&g->rec, (size_t)(desc->n_alloc > 0 ? desc->n_alloc : 1) * g->rec_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&g->ws, ws_bytes);
+  for (int a = 0; a < 3; ++a) g->nb[a] = ((desc->res[a] - 1) + (1 << kBlkShift) - 1) >> kBlkShift;
+  const size_t blk_bytes = (size_t)g->nb[0] * g->nb[1] * g->nb[2];
+  if (e == cudaSuccess) e = cudaMalloc(&g->blk, blk_bytes);
   if (e != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA,
                         "grid_create: allocation failed: %s", cudaGetErrorString(e)));
   e = cudaMemsetAsync(g->ws, 0, ws_bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->blk, 0, blk_bytes, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->links, links, (size_t)n_links * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cleanup(fail(PLX_ECUDA, "grid_create: %s", cudaGetErrorString(e)));
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
   k_check_links<<<grid_stride_blocks(n_links, g->num_sms), 256, 0, s>>>(g->links, n_links,
                                                                       desc->n_alloc, &ws->err);
+  k_build_blocks<<<grid_stride_blocks(n_links, g->num_sms), 256, 0, s>>>(
+      links, desc->res[0], desc->res[1], desc->res[2], g->blk, g->nb[0], g->nb[1]);
   if (desc->n_alloc > 0)
     k_repack<<<grid_stride_blocks(desc->n_alloc, g->num_sms), 256, 0, s>>>(
         density, sh, desc->n_alloc, desc->storage, g->rec);
@@ -254,6 +282,7 @@ plx_status plx_grid_destroy(plx_grid* g) {
   cudaError_t e = cudaDeviceSynchronize();
   cudaFree(g->links);
   cudaFree(g->rec);
+  cudaFree(g->blk);
   cudaFree(g->ws);
   delete g;
   if (e != cudaSuccess) return fail(PLX_ECUDA, "grid_destroy: %s", cudaGetErrorString(e));
@@ -293,6 +322,9 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
   std::memset(&P, 0, sizeof(P));
   P.g.links = g->links;
   P.g.rec = g->rec;
+  P.g.blk = g->blk;
+  P.g.nbx = g->nb[0];
+  P.g.nby = g->nb[1];
   P.g.rx = g->desc.res[0];
   P.g.ry = g->desc.res[1];
   P.g.rz = g->desc.res[2];

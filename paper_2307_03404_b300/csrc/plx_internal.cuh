@@ -51,11 +51,28 @@ struct RayList {
   int32_t fixed_cam;              // >= 0: every ray belongs to this camera
 };
 
+#ifndef PLX_BLK_SHIFT
+#define PLX_BLK_SHIFT 3
+#endif
+#ifndef PLX_FWD_MIN_BLOCKS
+#define PLX_FWD_MIN_BLOCKS 1
+#endif
+#ifndef PLX_BWD_MIN_BLOCKS
+#define PLX_BWD_MIN_BLOCKS 2
+#endif
+#ifndef PLX_POSE_MIN_BLOCKS
+#define PLX_POSE_MIN_BLOCKS 2
+#endif
+constexpr int kBlkShift = PLX_BLK_SHIFT;  // empty-space blocks of 2^shift cells per axis
+
 struct GridView {
   const int32_t* links;           // [rz][ry][rx]
   const void* rec;                // [n_alloc] records
+  const uint8_t* blk;             // [nbz][nby][nbx] 1 = some cell has an allocated corner;
+                                  // null = no block may be skipped
   int32_t rx, ry, rz;
   int32_t n_alloc;
+  int32_t nbx, nby;
   double lo[3];                   // box of the vertices
   double hi[3];
   double inv_h[3];                // 1 / spacing
@@ -143,6 +160,7 @@ __device__ __forceinline__ RayId ray_of(const Common& P, int64_t tile, int lane)
 struct RayF {
   float bh[3], bl[3];   // grid coords of sample 0: hi + lo parts
   float sh[3], sl[3];   // grid-coord increment per sample: hi + lo parts
+  float inv_s[3];       // 1 / increment (for block exits)
   float t0, dt;         // t of sample 0, step
   float dir[3];         // unit direction
   float org[3];         // camera centre
@@ -194,6 +212,7 @@ __device__ __forceinline__ void setup_ray(const Common& P, const RayId& id, RayF
     r.bl[a] = (float)(b - (double)r.bh[a]);
     r.sh[a] = (float)s;
     r.sl[a] = (float)(s - (double)r.sh[a]);
+    r.inv_s[a] = s != 0.0 ? (float)(1.0 / s) : 0.f;
     r.dir[a] = (float)d[a];
     r.org[a] = (float)o[a];
   }
@@ -332,6 +351,36 @@ __device__ __forceinline__ bool load_cell(const GridView& g, int ix, int iy, int
     }
   }
   return !any;
+}
+
+// Empty-space skipping. Samples whose cell lies in a block without any
+// allocated vertex contribute exactly nothing (sigma = 0 there), so the march
+// may jump over them; later samples keep their own index k, so nothing else
+// changes. Returns true if cell (ix, iy, iz) lies in such a block.
+__device__ __forceinline__ bool block_empty(const GridView& g, int ix, int iy, int iz) {
+  if (!g.blk) return false;
+  const int bx = ix >> kBlkShift, by = iy >> kBlkShift, bz = iz >> kBlkShift;
+  return __ldg(g.blk + ((int64_t)bz * g.nby + by) * g.nbx + bx) == 0;
+}
+
+// Index of the first sample that may lie outside the block of cell
+// (ix, iy, iz), never past it: the exit parameter along each axis is exact to
+// ~1e-6 samples (the distance to the block face is a Sterbenz-exact
+// difference), and 0.01 samples of margin keep the jump on the safe side.
+// Always > k.
+__device__ __forceinline__ int block_exit(const RayF& r, int ix, int iy, int iz, int k) {
+  const int c[3] = {ix, iy, iz};
+  float kmin = 3.0e38f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b = c[a] >> kBlkShift;
+    if (r.sh[a] > 0.f)
+      kmin = fminf(kmin, (((float)((b + 1) << kBlkShift) - r.bh[a]) - r.bl[a]) * r.inv_s[a]);
+    else if (r.sh[a] < 0.f)
+      kmin = fminf(kmin, (((float)(b << kBlkShift) - r.bh[a]) - r.bl[a]) * r.inv_s[a]);
+  }
+  const float kn = ceilf(kmin - 0.01f);
+  return kn > (float)k ? (kn < 2.0e9f ? (int)kn : 2000000000) : k + 1;
 }
 
 __device__ __forceinline__ void corner_weights(float fx, float fy, float fz, float w[8]) {

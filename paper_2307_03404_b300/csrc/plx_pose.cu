@@ -61,6 +61,11 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
     sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
     if (ix != cx || iy != cy || iz != cz) {
       cx = ix; cy = iy; cz = iz;
+      if (block_empty(P.g, ix, iy, iz)) {
+        empty = true;
+        k = block_exit(r, ix, iy, iz, k) - 1;
+        continue;
+      }
       empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
     }
     if (empty) continue;
@@ -118,10 +123,9 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
   D = SD;
 }
 
-// value index of H_ij (i <= j) in the per-ray vector
+// Per-ray values reduced: 21 of H (index below), 6 of b at 21..26, the loss at
+// 27 and the valid-ray count at 28. Value index of H_ij (i <= j):
 __host__ __device__ constexpr int hidx(int i, int j) { return i * 6 - i * (i - 1) / 2 + (j - i); }
-
-constexpr int kPoseValues = 29;  // 21 H + 6 b + loss + count
 
 // Warp reduce-scatter: v[0..31] per lane in, lane L returns sum over lanes of v[L].
 __device__ __forceinline__ double warp_reduce_scatter(const float v[32], int lane) {
@@ -150,7 +154,7 @@ __device__ __forceinline__ double warp_reduce_scatter(const float v[32], int lan
 }
 
 template <int STORE>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, PLX_POSE_MIN_BLOCKS)
 k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
                 const float* __restrict__ depth_t, double* __restrict__ partials,
                 unsigned int* __restrict__ retire, double* __restrict__ JtWJ,

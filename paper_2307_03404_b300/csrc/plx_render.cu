@@ -31,6 +31,7 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
   C[0] = C[1] = C[2] = 0.f;
   D = 0.f;
   T = 1.f;
+  n_all = r.n;
   for (int k = 0; k < r.n; ++k) {
     const float kf = (float)k;
     int ix, iy, iz;
@@ -40,9 +41,14 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
     sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
     if (ix != cx || iy != cy || iz != cz) {
       cx = ix; cy = iy; cz = iz;
+      if (block_empty(P.g, ix, iy, iz)) {
+        empty = true;
+        k = block_exit(r, ix, iy, iz, k) - 1;
+        continue;
+      }
       empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
     }
-    if (COUNT) { ++n_all; n_occ += empty ? 0 : 1; }
+    if (COUNT) n_occ += empty ? 0 : 1;
     if (empty) continue;
     float w[8];
     corner_weights(fx, fy, fz, w);
@@ -67,14 +73,17 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
     for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(wgt, col[ch], C[ch]);
     D = fmaf(wgt, t, D);
     T *= keep;
-    if (T < P.o.stop_T) break;
+    if (T < P.o.stop_T) {
+      n_all = k + 1;
+      break;
+    }
   }
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], C[ch]);
 }
 
 template <int STORE, bool COUNT>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, PLX_FWD_MIN_BLOCKS)
 k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __restrict__ depth,
           float* __restrict__ state, int32_t* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
@@ -150,6 +159,11 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
       if (dirty) flush_cell(grad, l, gs, gc, Y);
       dirty = false;
       cx = ix; cy = iy; cz = iz;
+      if (block_empty(P.g, ix, iy, iz)) {
+        empty = true;
+        k = block_exit(r, ix, iy, iz, k) - 1;
+        continue;
+      }
       empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
 #pragma unroll
       for (int c = 0; c < 8; ++c) { gs[c] = 0.f; gc[c][0] = gc[c][1] = gc[c][2] = 0.f; }
@@ -210,7 +224,7 @@ __global__ void k_count_valid(const float* __restrict__ depth_t, int64_t n,
 }
 
 template <int STORE>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, PLX_BWD_MIN_BLOCKS)
 k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
                 const float* __restrict__ depth_t, const float* __restrict__ rgb,
                 const float* __restrict__ depth, float* __restrict__ grad,

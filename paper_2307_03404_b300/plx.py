@@ -18,7 +18,7 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libplx.so")
+LIB_PATH = os.environ.get("PLX_LIBRARY") or os.path.join(_HERE, "libplx.so")
 
 STORE_F32, STORE_BF16, STORE_F16, STORE_F32_BF16 = 0, 1, 2, 3
 STORAGE = {"f32": STORE_F32, "bf16": STORE_BF16, "f16": STORE_F16, "f32_bf16": STORE_F32_BF16}
