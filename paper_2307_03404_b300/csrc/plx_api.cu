@@ -81,6 +81,12 @@ static plx_status launch_check(const char* what) {
 
 static int record_bytes(int storage) { return storage == PLX_STORE_F32 ? 128 : 64; }
 
+// A double as an unevaluated (hi, lo) sum of two floats.
+static float2 split_ff(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 // ----------------------------------------------------------- repack kernels
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
@@ -333,9 +339,16 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
     P.g.lo[a] = g->desc.lo[a];
     P.g.hi[a] = g->desc.hi[a];
     P.g.inv_h[a] = g->inv_h[a];
+    P.g.lo_ff[a] = split_ff(g->desc.lo[a]);
+    P.g.inv_h_ff[a] = split_ff(g->inv_h[a]);
+    P.g.ext[a] = (float)(g->desc.res[a] - 1);
   }
   P.o.step = o->step;
   P.o.near_t = o->near_t;
+  P.o.step_ff = split_ff(o->step);
+  P.o.half_step_ff = split_ff(0.5 * o->step);
+  P.o.inv_step_ff = split_ff(1.0 / o->step);
+  P.o.near_ff = split_ff(o->near_t);
   P.o.stop_T = (float)o->stop_T;
   P.o.step_f = (float)o->step;
   for (int c = 0; c < 3; ++c) P.o.bg[c] = o->bg[c];
@@ -354,10 +367,10 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
     if (!(in.fx != 0.0) || !(in.fy != 0.0) || !std::isfinite(in.fx) || !std::isfinite(in.fy))
       return fail(PLX_EINVAL, "%s: camera %d focal length", what, c);
     CamParam& cp = P.ct.cam[c];
-    cp.inv_fx = 1.0 / in.fx;
-    cp.inv_fy = 1.0 / in.fy;
-    cp.cx = in.cx;
-    cp.cy = in.cy;
+    cp.inv_fx = split_ff(1.0 / in.fx);
+    cp.inv_fy = split_ff(1.0 / in.fy);
+    cp.cx = split_ff(in.cx);
+    cp.cy = split_ff(in.cy);
     cp.width = in.width;
     cp.height = in.height;
     cp.tiles_x = (in.width + kTileW - 1) / kTileW;

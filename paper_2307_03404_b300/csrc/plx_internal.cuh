@@ -29,7 +29,7 @@ constexpr int kRecordSlots = 32;      // record = 32 slots (28 used)
 
 // ---------------------------------------------------------------- params
 struct CamParam {
-  double inv_fx, inv_fy, cx, cy;  // 1/fx, 1/fy, principal point
+  float2 inv_fx, inv_fy, cx, cy;  // 1/fx, 1/fy, principal point as (hi, lo) float pairs
   int32_t width, height;
   int64_t ray_off;                // dense mode: index of the camera's ray 0
   int64_t tile_off;               // dense mode: index of the camera's tile 0
@@ -76,10 +76,14 @@ struct GridView {
   double lo[3];                   // box of the vertices
   double hi[3];
   double inv_h[3];                // 1 / spacing
+  float2 lo_ff[3];                // lo as (hi, lo) float pairs
+  float2 inv_h_ff[3];             // 1 / spacing as (hi, lo) float pairs
+  float ext[3];                   // res - 1: the box in grid coordinates is [0, ext]
 };
 
 struct Opts {
   double step, near_t;
+  float2 step_ff, half_step_ff, inv_step_ff, near_ff;  // (hi, lo) float pairs
   float stop_T;
   float step_f;
   float bg[3];
@@ -155,8 +159,48 @@ __device__ __forceinline__ RayId ray_of(const Common& P, int64_t tile, int lane)
 }
 
 // ------------------------------------------------------------ ray setup
-// Per ray, in FP64: direction, box clip, sample count, and the grid-space
-// position of sample k as b + k*s in float-float form.
+// Float-float arithmetic: a value is an unevaluated sum hi + lo of two floats
+// (about 44 significant bits). Built from error-free transformations (Knuth's
+// two-sum, the FMA product error), it gives the per-ray set-up the accuracy
+// it needs on the FP32 pipes; FP64 is slow on this part.
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff ffv(float h, float l = 0.f) { ff r; r.h = h; r.l = l; return r; }
+__device__ __forceinline__ ff ffv(float2 v) { return ffv(v.x, v.y); }
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return ffv(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+  const float s = a + b;
+  return ffv(s, b - (s - a));
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  const float p = a * b;
+  return ffv(p, fmaf(a, b, -p));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ffv(-a.h, -a.l); }
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return quick_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = two_prod(a.h, b.h);
+  p.l = fmaf(a.h, b.l, fmaf(a.l, b.h, p.l));
+  return quick_two_sum(p.h, p.l);
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  const float q = __fdividef(a.h, b.h);
+  const ff r = ff_sub(a, ff_mul(ffv(q), b));
+  return quick_two_sum(q, __fdividef(r.h, b.h));
+}
+__device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+
+// Per ray: direction, box clip, sample count, and the grid-space position of
+// sample k as b + k*s, handed to the sample loop as float pairs.
 struct RayF {
   float bh[3], bl[3];   // grid coords of sample 0: hi + lo parts
   float sh[3], sl[3];   // grid-coord increment per sample: hi + lo parts
@@ -168,57 +212,99 @@ struct RayF {
   int n;                // samples to march
 };
 
-__device__ __forceinline__ void setup_ray(const Common& P, const RayId& id, RayF& r) {
+// Must be called by all 32 lanes of the warp (id.cam valid on every lane).
+__device__ __forceinline__ void setup_ray(const Common& P, const RayId& id, RayF& r, int lane) {
+  // the pose [R | o] as float pairs: converted once per warp when the warp
+  // shares a camera (always in dense mode), else by each lane
+  float Ph[12], Pl[12];
+  const int cam0 = __shfl_sync(0xffffffffu, id.cam, 0);
+  if (__all_sync(0xffffffffu, id.cam == cam0)) {
+    const double v = __ldg(P.poses + 12 * cam0 + (lane < 12 ? lane : 0));
+    const float vh = (float)v, vl = (float)(v - (double)vh);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      Ph[j] = __shfl_sync(0xffffffffu, vh, j);
+      Pl[j] = __shfl_sync(0xffffffffu, vl, j);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const double v = __ldg(P.poses + 12 * id.cam + j);
+      Ph[j] = (float)v;
+      Pl[j] = (float)(v - (double)Ph[j]);
+    }
+  }
   const CamParam& cp = P.ct.cam[id.cam];
-  const double* T = P.poses + 12 * id.cam;
-  const double dcx = ((double)id.u + 0.5 - cp.cx) * cp.inv_fx;
-  const double dcy = ((double)id.v + 0.5 - cp.cy) * cp.inv_fy;
-  const double n2 = dcx * dcx + dcy * dcy + 1.0;
-  const double inv_n = rsqrt(n2);
-  double d[3], o[3];
+  // d_c = ((u + 1/2 - cx) / fx, (v + 1/2 - cy) / fy, 1), normalised
+  const ff x = ff_mul(ff_sub(ffv((float)id.u + 0.5f), ffv(cp.cx)), ffv(cp.inv_fx));
+  const ff y = ff_mul(ff_sub(ffv((float)id.v + 0.5f), ffv(cp.cy)), ffv(cp.inv_fy));
+  const ff n2 = ff_add(ff_add(ff_mul(x, x), ff_mul(y, y)), ffv(1.f));
+  const float y0 = rsqrtf(n2.h);
+  const ff e = ff_sub(ffv(1.f), ff_mul(n2, two_prod(y0, y0)));  // 1 - n2 y0^2
+  const ff inv_n = quick_two_sum(y0, 0.5f * y0 * e.h);           // one Newton step
+  const ff dcn[3] = {ff_mul(x, inv_n), ff_mul(y, inv_n), inv_n};
+  ff og[3], dg[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    d[a] = (__ldg(T + 4 * a) * dcx + __ldg(T + 4 * a + 1) * dcy + __ldg(T + 4 * a + 2)) * inv_n;
-    o[a] = __ldg(T + 4 * a + 3);
+    const ff d = ff_add(ff_add(ff_mul(ffv(Ph[4 * a], Pl[4 * a]), dcn[0]),
+                               ff_mul(ffv(Ph[4 * a + 1], Pl[4 * a + 1]), dcn[1])),
+                        ff_mul(ffv(Ph[4 * a + 2], Pl[4 * a + 2]), dcn[2]));
+    const ff o = ffv(Ph[4 * a + 3], Pl[4 * a + 3]);
+    og[a] = ff_mul(ff_sub(o, ffv(P.g.lo_ff[a])), ffv(P.g.inv_h_ff[a]));
+    dg[a] = ff_mul(d, ffv(P.g.inv_h_ff[a]));
+    r.dir[a] = d.h;
+    r.org[a] = o.h;
   }
-  // slab clip
-  double tn = -1e300, tf = 1e300;
+  // slab clip against [0, ext] in grid coordinates (t is still the world
+  // distance along the unit direction); the binding planes are found in FP32
+  // and their crossing parameters recomputed in float-float
+  float tn = -3.0e38f, tf = 3.0e38f;
+  int ina = -1, outa = -1;
+  float inb = 0.f, outb = 0.f;
   bool hit = true;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (d[a] != 0.0) {
-      const double inv = 1.0 / d[a];
-      double ta = (P.g.lo[a] - o[a]) * inv, tb = (P.g.hi[a] - o[a]) * inv;
-      if (ta > tb) { const double s = ta; ta = tb; tb = s; }
-      tn = fmax(tn, ta);
-      tf = fmin(tf, tb);
-    } else if (o[a] < P.g.lo[a] || o[a] > P.g.hi[a]) {
+    if (fabsf(dg[a].h) > 1e-30f) {
+      const float inv = 1.f / dg[a].h;
+      float b0 = 0.f, b1 = P.g.ext[a];
+      if (inv < 0.f) { b0 = P.g.ext[a]; b1 = 0.f; }
+      const float t0 = (b0 - og[a].h) * inv, t1 = (b1 - og[a].h) * inv;
+      if (t0 > tn) { tn = t0; ina = a; inb = b0; }
+      if (t1 < tf) { tf = t1; outa = a; outb = b1; }
+    } else if (og[a].h < 0.f || og[a].h > P.g.ext[a]) {
       hit = false;
     }
   }
-  tn = fmax(tn, P.o.near_t);
-  int n = 0;
-  if (hit && tf > tn) {
-    const double cnt = floor((tf - tn) / P.o.step);
-    n = (int)fmin(cnt, (double)P.o.max_samples);
-  }
-  r.n = n;
-  const double t0 = tn + 0.5 * P.o.step;
+  ff t_enter = ffv(-3.0e38f), t_exit = ffv(3.0e38f);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double b = (o[a] + t0 * d[a] - P.g.lo[a]) * P.g.inv_h[a];
-    const double s = P.o.step * d[a] * P.g.inv_h[a];
-    r.bh[a] = (float)b;
-    r.bl[a] = (float)(b - (double)r.bh[a]);
-    r.sh[a] = (float)s;
-    r.sl[a] = (float)(s - (double)r.sh[a]);
-    r.inv_s[a] = s != 0.0 ? (float)(1.0 / s) : 0.f;
-    r.dir[a] = (float)d[a];
-    r.org[a] = (float)o[a];
+    if (a == ina) t_enter = ff_div(ff_sub(ffv(inb), og[a]), dg[a]);
+    if (a == outa) t_exit = ff_div(ff_sub(ffv(outb), og[a]), dg[a]);
   }
-  r.t0 = n > 0 ? (float)t0 : 0.f;
+  const ff near_t = ffv(P.o.near_ff);
+  const ff t_min = ff_gt(near_t, t_enter) ? near_t : t_enter;
+  int n = 0;
+  if (hit && ff_gt(t_exit, t_min)) {
+    const ff cnt = ff_mul(ff_sub(t_exit, t_min), ffv(P.o.inv_step_ff));
+    float fl = floorf(cnt.h);
+    if (fl == cnt.h && cnt.l < 0.f) fl -= 1.f;
+    n = (int)fminf(fl, (float)P.o.max_samples);
+  }
+  r.n = n;
+  const ff t0 = ff_add(t_min, ffv(P.o.half_step_ff));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const ff b = ff_add(og[a], ff_mul(t0, dg[a]));
+    const ff st = ff_mul(ffv(P.o.step_ff), dg[a]);
+    r.bh[a] = b.h;
+    r.bl[a] = b.l;
+    r.sh[a] = st.h;
+    r.sl[a] = st.l;
+    r.inv_s[a] = st.h != 0.f ? 1.f / st.h : 0.f;
+  }
+  r.t0 = n > 0 ? t0.h : 0.f;
   r.dt = P.o.step_f;
-  r.dc_norm = (float)sqrt(n2);
+  r.dc_norm = n2.h * inv_n.h;
 }
 
 // Real SH of degree 0..2 (orthonormal; order 1; y, z, x; xy, yz, 3z^2-1,

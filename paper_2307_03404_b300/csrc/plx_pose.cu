@@ -14,11 +14,11 @@
 //   dX/drho = dX/do,  dX/dphi = o x dX/do + d x dX/dd.
 //
 // Reduction: per ray 29 values (21 of J^T W J, 6 of J^T W r, r^T W r, valid
-// count) are formed in FP32 from the FP32 Jacobian and summed in FP64 from the
-// first addition on: a warp reduce-scatter leaves lane L with the warp's sum of
-// value L, each lane keeps one FP64 accumulator across the rays it visits, and
-// blocks write FP64 partials that the last block to finish sums in a fixed
-// order. The result is deterministic.
+// count) are formed in FP32 from the FP32 Jacobian. A warp reduce-scatter in
+// compensated float-float arithmetic leaves lane L with the warp's sum of
+// value L; from there everything is FP64: each lane keeps one FP64
+// accumulator across the rays it visits, and blocks write FP64 partials that
+// the last block to finish sums in a fixed order. The result is deterministic.
 #include "plx_internal.cuh"
 
 namespace plx {
@@ -127,17 +127,19 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
 // 27 and the valid-ray count at 28. Value index of H_ij (i <= j):
 __host__ __device__ constexpr int hidx(int i, int j) { return i * 6 - i * (i - 1) / 2 + (j - i); }
 
-// Warp reduce-scatter: v[0..31] per lane in, lane L returns sum over lanes of v[L].
+// Warp reduce-scatter of v[0..31]: lane L returns the sum over the warp of
+// v[L]. Sums are carried as float-float pairs (about 44 significant bits), so
+// the FP32 pipes do the work and the FP64 pipe, slow on this part, is used
+// once per lane at the end.
 __device__ __forceinline__ double warp_reduce_scatter(const float v[32], int lane) {
-  double a[16];
+  ff a[16];
   {
     const bool up = lane & 16;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const float send = up ? v[i] : v[i + 16];
       const float keep = up ? v[i + 16] : v[i];
-      const float recv = __shfl_xor_sync(0xffffffffu, send, 16);
-      a[i] = (double)keep + (double)recv;
+      a[i] = two_sum(keep, __shfl_xor_sync(0xffffffffu, send, 16));
     }
   }
 #pragma unroll
@@ -145,12 +147,14 @@ __device__ __forceinline__ double warp_reduce_scatter(const float v[32], int lan
     const bool up = lane & off;
 #pragma unroll
     for (int i = 0; i < off; ++i) {
-      const double send = up ? a[i] : a[i + off];
-      const double keep = up ? a[i + off] : a[i];
-      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      const ff send = up ? a[i] : a[i + off];
+      const ff keep = up ? a[i + off] : a[i];
+      const ff recv = ffv(__shfl_xor_sync(0xffffffffu, send.h, off),
+                          __shfl_xor_sync(0xffffffffu, send.l, off));
+      a[i] = ff_add(keep, recv);
     }
   }
-  return a[0];
+  return (double)a[0].h + (double)a[0].l;
 }
 
 template <int STORE>
@@ -171,11 +175,11 @@ k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = 0.f;
     const RayId id = ray_of(P, tile, lane);
+    RayF r;
+    setup_ray(P, id, r, lane);
     float dz = 0.f;
     if (id.valid) dz = __ldg(depth_t + id.out);
     if (id.valid && depth_valid(dz)) {
-      RayF r;
-      setup_ray(P, id, r);
       float Y[9];
       sh_basis(r.dir, Y);
       PoseAcc A;

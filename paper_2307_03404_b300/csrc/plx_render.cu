@@ -88,8 +88,10 @@ k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __re
           float* __restrict__ state, int32_t* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
   const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (tile >= P.ct.n_tiles) return;
+  if (tile >= P.ct.n_tiles) return;  // whole warps only
   const RayId id = ray_of(P, tile, lane);
+  RayF r;
+  setup_ray(P, id, r, lane);
   if (!id.valid) {
     if (!P.ct.dense && id.out < P.ct.n_rays) {  // bad list entry: loud NaN output
       const float nan = __int_as_float(0x7fc00000);
@@ -98,8 +100,6 @@ k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __re
     }
     return;
   }
-  RayF r;
-  setup_ray(P, id, r);
   float Y[9];
   sh_basis(r.dir, Y);
   float C[3], D, T;
@@ -229,50 +229,46 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
                 const float* __restrict__ depth_t, const float* __restrict__ rgb,
                 const float* __restrict__ depth, float* __restrict__ grad,
                 double* __restrict__ loss_out, const unsigned long long* __restrict__ Mc) {
-  __shared__ double red[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  double loss = 0.0;
+  float loss = 0.f;
   if (tile < P.ct.n_tiles) {
     const RayId id = ray_of(P, tile, lane);
+    RayF r;
+    setup_ray(P, id, r, lane);
     const unsigned long long M = *Mc;
     if (id.valid && M > 0) {
       const float dz = __ldg(depth_t + id.out);
       if (depth_valid(dz)) {
-        RayF r;
-        setup_ray(P, id, r);
         float Y[9];
         sh_basis(r.dir, Y);
         const float invM = (float)(1.0 / (double)M);
         const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
         float Cf[3], gC[3];
-        double e2 = 0.0;
+        float e2 = 0.f;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
           Cf[ch] = __ldg(rgb + 3 * id.out + ch);
           const float e = Cf[ch] - __ldg(rgb_t + 3 * id.out + ch);
-          e2 += (double)e * (double)e;
+          e2 = fmaf(e, e, e2);
           gC[ch] = 2.f * e * invM;
         }
         const float Df = __ldg(depth + id.out);
         const float eD = Df - Dt;
-        loss = (e2 + (double)P.o.lambda_d * (double)eD * (double)eD) / (double)M;
+        loss = fmaf(P.o.lambda_d * eD, eD, e2);
         const float gD = 2.f * P.o.lambda_d * eD * invM;
         march_backward<STORE>(P, r, Y, Cf, Df, gC, gD, grad);
       }
     }
   }
   if (loss_out) {
+    // per warp: FP64 sum of the rays' squared residuals, one atomic per warp
+    double s = (double)loss;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, off);
-    if (lane == 0) red[warp] = loss;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int i = 0; i < kWarpsPerBlock; ++i) s += red[i];
-      if (s != 0.0) atomicAdd(loss_out, s);
-      if (blockIdx.x == 0) loss_out[1] = (double)*Mc;
-    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const unsigned long long M = *Mc;
+    if (lane == 0 && s != 0.0) atomicAdd(loss_out, s / (double)M);
+    if (blockIdx.x == 0 && threadIdx.x == 0) loss_out[1] = (double)M;
   }
 }
 
