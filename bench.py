@@ -42,10 +42,48 @@ def shard_frames(world: int, rank: int, per_rank: int = FRAMES_PER_RANK):
     return list(range(rank * per_rank, (rank + 1) * per_rank))
 
 
+def rank_max(x: float, world: int, device) -> float:
+    """Maximum of ``x`` over all ranks (host-side timing only; not on the data
+    path)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def combine_rank_times(times_ms, units_per_rank):
     """Whole-job throughput: all ranks' units over the slowest rank's time."""
     t = max(times_ms)
     return sum(units_per_rank) / (t / 1e3), t
+
+
+def kernel_source_sha():
+    """Hash of the CUDA sources: a DRAM-traffic record taken with ncu applies
+    only to the kernels it was measured on."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2307_03404_b300", "csrc", "*.cu*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload, storage):
+    """DRAM bytes per launch from profiles/traffic.json if it was taken on the
+    current kernel sources, else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    for rec in json.load(open(p)):
+        if (rec["kernel"] == kernel and rec["workload"] == workload
+                and rec["storage"] == storage and rec["source_sha"] == kernel_source_sha()):
+            return rec["dram_bytes_per_launch"]
+    return None
 
 
 def peaks():
@@ -247,16 +285,9 @@ def run_ours(args):
     clocks = clk.summary()
 
     # whole-job numbers: max over ranks
-    def rank_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    t_main = rank_max(sum(main["step_ms"]))
-    t_e2e = rank_max(sum(main["e2e_ms"]))
-    t_other = rank_max(sum(other["step_ms"]))
+    t_main = rank_max(sum(main["step_ms"]), world, "cuda")
+    t_e2e = rank_max(sum(main["e2e_ms"]), world, "cuda")
+    t_other = rank_max(sum(other["step_ms"]), world, "cuda")
     rays_job = n_rays * world * K
     value = rays_job / (t_main / 1e3)
 
@@ -281,6 +312,9 @@ def run_ours(args):
     step_roof = (fwd_b + bwd_b) / (hbm * 1e9) * 1e3   # ms per step at the HBM roof
     fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage)
 
+    traffic = measured_traffic(dom, "room256", args.storage)
+    if traffic:
+        dram_gbs = traffic / (dom_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": t_main / K, "higher_is_better": True, "scaling": "weak",
@@ -288,10 +322,18 @@ def run_ours(args):
         "config": dict(workload_config(sc, cams_np, args.storage),
                        parallelism=f"replicated grid, keyframes sharded over {world} rank(s)"),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": measured_traffic(dom, "room256", args.storage),
+                     "model": "no-reuse byte model: 32 B of links per marched sample and pass, "
+                              "896 B (f32) / 448 B (16-bit) per gathered sample with an "
+                              "allocated corner, 1792 B of FP32 gradient RMW per such sample "
+                              "in the adjoint, 32-36 B of per-ray I/O; frac > 1 = beating "
+                              "the no-reuse bound through L1/L2 reuse",
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_per_launch": dom_b, "ms_per_launch": dom_ms,
                      "step_frac": step_roof / (t_main / K),
+                     "dram_gbs": dram_gbs if traffic else None,
+                     "dram_frac": dram_gbs / hbm if traffic else None,
                      "S_all_mean": s_all, "S_occ_mean": s_occ},
         "e2e": {"value": rays_job / (t_e2e / 1e3), "unit": "rays/s",
                 "h2d_bytes_per_step": main["h2d"], "d2h_bytes_per_step": main["d2h"]},
@@ -302,6 +344,7 @@ def run_ours(args):
                         "step_frac": (fo_b + bo_b) / (hbm * 1e9) * 1e3 / (t_other / K)},
         "loss": main["loss"],
         "kernels_ms": {"forward": fwd_ms, "backward_grid": bwd_ms},
+        "kernel_source_sha": kernel_source_sha(),
     }
     if not args.no_tracking:
         line["tracking"] = run_tracking(args, world, rank, barrier)
@@ -370,6 +413,7 @@ def run_tracking(args, world, rank, barrier):
         err = float(np.abs(pose.cpu().numpy().reshape(3, 4) - cam.T_wc).max())
         out[storage] = {"value": iters * len(ms) / (sum(ms) / 1e3),
                         "ms_per_iter": sum(ms) / len(ms) / iters,
+                        "start_pose_err": float(np.abs(T0 - cam.T_wc).max()),
                         "final_pose_err": err, "final_loss": float(loss[0].item())}
         grid.close()
     out["value"] = out["f32"]["value"]

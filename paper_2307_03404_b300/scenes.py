@@ -96,8 +96,8 @@ def look_at(eye, target, up=(0.0, 1.0, 0.0)) -> np.ndarray:
 
 
 def perturb_pose(T_wc, trans_m: float, rot_deg: float, rng) -> np.ndarray:
-    """Move a pose by ``trans_m`` along a random unit axis and rotate it by
-    ``rot_deg`` about a random axis (world frame, left)."""
+    """Move a camera by ``trans_m`` along a random unit axis and turn it by
+    ``rot_deg`` about a random axis through its own centre."""
     from scipy.spatial.transform import Rotation
 
     T = np.asarray(T_wc, np.float64).reshape(3, 4)
@@ -108,7 +108,7 @@ def perturb_pose(T_wc, trans_m: float, rot_deg: float, rng) -> np.ndarray:
     Rp = Rotation.from_rotvec(np.deg2rad(rot_deg) * a).as_matrix()
     out = np.zeros((3, 4))
     out[:, :3] = Rp @ T[:, :3]
-    out[:, 3] = Rp @ T[:, 3] + trans_m * u
+    out[:, 3] = T[:, 3] + trans_m * u
     return out
 
 
@@ -257,28 +257,40 @@ def _random_prims(rng, room_lo, room_hi, n):
 
 
 def _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims, margin_vox=12):
-    """Signed distance (positive in free space) at every vertex: walls are the
-    faces of the room box (solid outside it). Each primitive is evaluated only
-    within ``margin_vox`` voxels of its extent; farther away its distance
-    exceeds any band width used here, so the band is unchanged."""
+    """Signed distance (positive in free space) at every vertex, and the id of
+    the nearest surface (0..5 the walls -x, +x, -y, +y, -z, +z; 6 + i primitive
+    i). Walls are the faces of the room box (solid outside it). Each primitive
+    is evaluated only within ``margin_vox`` voxels of its extent; farther away
+    its distance exceeds any band width used here, so the band is unchanged."""
     xs = np.linspace(lo[0], hi[0], R).astype(np.float32)
     ys = np.linspace(lo[1], hi[1], R).astype(np.float32)
     zs = np.linspace(lo[2], hi[2], R).astype(np.float32)
-    wx = np.minimum(xs - room_lo[0], room_hi[0] - xs).astype(np.float32)
-    wy = np.minimum(ys - room_lo[1], room_hi[1] - ys).astype(np.float32)
-    wz = np.minimum(zs - room_lo[2], room_hi[2] - zs).astype(np.float32)
+
+    def wall(v, a):
+        lo_d, hi_d = v - room_lo[a], room_hi[a] - v
+        return np.minimum(lo_d, hi_d).astype(np.float32), (hi_d < lo_d).astype(np.uint8)
+
+    (wx, sx), (wy, sy), (wz, sz) = wall(xs, 0), wall(ys, 1), wall(zs, 2)
     s = np.empty((R, R, R), np.float32)
-    np.minimum(wz[:, None, None], wy[None, :, None], out=s)
-    np.minimum(s, wx[None, None, :], out=s)
+    ids = np.empty((R, R, R), np.uint8)
+    for k in range(R):          # slab by slab keeps the temporaries small
+        sl = np.minimum(wy[:, None], wx[None, :])
+        idl = np.where(wy[:, None] <= wx[None, :], 2 + sy[:, None], 0 + sx[None, :])
+        zsel = wz[k] <= sl
+        s[k] = np.where(zsel, wz[k], sl)
+        ids[k] = np.where(zsel, 4 + sz[k], idl)
     h = (hi - lo) / (R - 1)
-    for p in prims:
+    for i, p in enumerate(prims):
         ext = _prim_extent(p) + margin_vox * h
         i0 = np.clip(np.floor((p["c"] - ext - lo) / h).astype(int), 0, R - 1)
         i1 = np.clip(np.ceil((p["c"] + ext - lo) / h).astype(int) + 1, 0, R)
         sub = s[i0[2]:i1[2], i0[1]:i1[1], i0[0]:i1[0]]
-        np.minimum(sub, _prim_sdf_sep(xs[i0[0]:i1[0]], ys[i0[1]:i1[1]], zs[i0[2]:i1[2]], p),
-                   out=sub)
-    return s
+        isub = ids[i0[2]:i1[2], i0[1]:i1[1], i0[0]:i1[0]]
+        d = _prim_sdf_sep(xs[i0[0]:i1[0]], ys[i0[1]:i1[1]], zs[i0[2]:i1[2]], p)
+        closer = d < sub
+        sub[closer] = d[closer]
+        isub[closer] = 6 + i
+    return s, ids
 
 
 def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 3.2,
@@ -289,7 +301,10 @@ def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 
     ``occupancy`` of all vertices (distance ties broken by a seeded jitter of
     +-0.05 voxel); the ``border`` outermost vertex layers are never allocated.
     Allocated density rises across the band into the solid, about 0.6 / h at
-    the inner band edge and slightly negative at the outer one; SH ~ N(0, 0.3).
+    the inner band edge and slightly negative at the outer one. SH: each
+    surface (wall or primitive) has its own N(0, 0.28) coefficients, and each
+    vertex adds N(0, 0.1) to those of its nearest surface (about N(0, 0.3)
+    overall): surfaces carry a colour with texture, as scanned rooms do.
     """
     rng = np.random.default_rng(seed)
     lo = np.full(3, -half)
@@ -299,7 +314,7 @@ def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 
     room_lo = lo + wall_inset_vox * h
     room_hi = hi - wall_inset_vox * h
     prims = _random_prims(rng, room_lo, room_hi, n_prims)
-    s = _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims)
+    s, ids = _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims)
     b = border
     key = np.abs(s)
     key += (rng.random(key.shape, dtype=np.float32) - np.float32(0.5)) * np.float32(0.1 * hm)
@@ -315,12 +330,15 @@ def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 
     links[sel] = np.arange(n, dtype=np.int32)
     links = links.reshape(R, R, R)
     sv = s.reshape(-1)[sel].astype(np.float64)
-    del s
+    surf = ids.reshape(-1)[sel]
+    del s, ids
     w = max(float(np.abs(sv).max()), hm)
     density = ((0.6 / hm) * (0.5 - 0.6 * sv / w)
                + (0.05 / hm) * rng.standard_normal(n)).astype(np.float32)
+    base = (0.28 * rng.standard_normal((6 + len(prims), N_SH))).astype(np.float32)
     sh = rng.standard_normal((n, N_SH), dtype=np.float32)
-    sh *= np.float32(0.3)
+    sh *= np.float32(0.1)
+    sh += base[surf]
     grid = Grid((R, R, R), lo, hi, links, density, sh)
     return Scene(grid, prims, room_lo, room_hi)
 
