@@ -373,14 +373,14 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
     cp.cy = split_ff(in.cy);
     cp.width = in.width;
     cp.height = in.height;
-    cp.tiles_x = (in.width + kTileW - 1) / kTileW;
-    const int tiles_y = (in.height + kTileH - 1) / kTileH;
+    cp.supers_x = (in.width + kTileW * kSuperW - 1) / (kTileW * kSuperW);
+    const int supers_y = (in.height + kTileH * kSuperH - 1) / (kTileH * kSuperH);
     const bool use = fixed_cam < 0 || fixed_cam == c;
     cp.ray_off = ray_off;
     cp.tile_off = tile_off;
     if (use) {
       ray_off += (int64_t)in.width * in.height;
-      tile_off += (int64_t)cp.tiles_x * tiles_y;
+      tile_off += (int64_t)cp.supers_x * supers_y * kSuperW * kSuperH;
     }
   }
   const bool dense = rays->pixel == nullptr;

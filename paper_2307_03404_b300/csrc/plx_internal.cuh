@@ -23,6 +23,8 @@ namespace plx {
 
 constexpr int kTileW = 8;             // dense-mode warp tile: 8 x 4 pixels
 constexpr int kTileH = 4;
+constexpr int kSuperW = 2;            // a block's 8 warp tiles form a 16 x 16 supertile
+constexpr int kSuperH = 4;
 constexpr int kBlock = 256;           // threads per block of the ray kernels
 constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kRecordSlots = 32;      // record = 32 slots (28 used)
@@ -33,7 +35,7 @@ struct CamParam {
   int32_t width, height;
   int64_t ray_off;                // dense mode: index of the camera's ray 0
   int64_t tile_off;               // dense mode: index of the camera's tile 0
-  int32_t tiles_x;                // tiles per row
+  int32_t supers_x;               // 16x16 supertiles per row
   int32_t pad;
 };
 
@@ -126,8 +128,13 @@ __device__ __forceinline__ RayId ray_of(const Common& P, int64_t tile, int lane)
   if (P.ct.dense) {
     const int c = P.rl.fixed_cam >= 0 ? P.rl.fixed_cam : find_cam(P.ct, tile);
     const CamParam& cp = P.ct.cam[c];
+    // tiles are numbered supertile by supertile (8 per 16x16 pixels), so the
+    // 8 warps of a block march neighbouring rays and share grid vertices
     const int64_t lt = tile - cp.tile_off;
-    const int ty = (int)(lt / cp.tiles_x), tx = (int)(lt - (int64_t)ty * cp.tiles_x);
+    const int64_t st = lt >> 3;
+    const int sub = (int)(lt & 7);
+    const int sty = (int)(st / cp.supers_x), stx = (int)(st - (int64_t)sty * cp.supers_x);
+    const int tx = stx * kSuperW + (sub % kSuperW), ty = sty * kSuperH + (sub / kSuperW);
     r.cam = c;
     r.u = tx * kTileW + (lane & (kTileW - 1));
     r.v = ty * kTileH + (lane / kTileW);
@@ -467,6 +474,29 @@ __device__ __forceinline__ int block_exit(const RayF& r, int ix, int iy, int iz,
   }
   const float kn = ceilf(kmin - 0.01f);
   return kn > (float)k ? (kn < 2.0e9f ? (int)kn : 2000000000) : k + 1;
+}
+
+// Same as load_cell, with the corner cache in shared memory: slot s of the
+// calling thread is sc[s * kBlock] (s = 4c: density of corner c, 4c+1+ch: its
+// projected colour), so the lanes of a warp hit distinct banks.
+template <int STORE>
+__device__ __forceinline__ bool load_cell_smem(const GridView& g, int ix, int iy, int iz,
+                                               const float Y[9], int32_t l[8], float* sc) {
+  load_links(g, ix, iy, iz, l);
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float sig = 0.f, col[3] = {0.f, 0.f, 0.f};
+    if (l[c] >= 0) {
+      any = true;
+      load_corner<STORE>(g.rec, l[c], Y, sig, col);
+    }
+    sc[(4 * c) * kBlock] = sig;
+    sc[(4 * c + 1) * kBlock] = col[0];
+    sc[(4 * c + 2) * kBlock] = col[1];
+    sc[(4 * c + 3) * kBlock] = col[2];
+  }
+  return !any;
 }
 
 __device__ __forceinline__ void corner_weights(float fx, float fy, float fz, float w[8]) {
