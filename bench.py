@@ -348,6 +348,8 @@ def run_ours(args):
     }
     if not args.no_tracking:
         line["tracking"] = run_tracking(args, world, rank, barrier)
+    if not args.no_batch:
+        line["batched"] = run_batch_bench(args, barrier)
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(sc, cams_np, rgb_np, depth_np, opts, args.cpu_seconds)
     if rank == 0:
@@ -417,6 +419,90 @@ def run_tracking(args, world, rank, barrier):
                         "final_pose_err": err, "final_loss": float(loss[0].item())}
         grid.close()
     out["value"] = out["f32"]["value"]
+    return out
+
+
+def run_batch_bench(args, barrier):
+    """64 frames of mixed sizes (32 mapping, 32 tracking) on a 512^3 grid in one
+    persistent launch, against the same work through the separate calls."""
+    import torch
+
+    from paper_2307_03404_b300 import plx, scenes
+
+    R, occ, npr, seed = scenes.WORKLOADS["room512mix"]
+    t = time.time()
+    sc = scenes.room_scene(R, occ, npr, seed)
+    cams_np = scenes.mixed_resolution_cameras(sc, 64, seed + 1)
+    rgb_np, depth_np = scenes.sensor_frames(sc, cams_np, seed + 2)
+    log(f"[bench] room512mix scene + 64 frames in {time.time() - t:.1f}s")
+    work = [(i, plx.WORK_MAP if i % 2 == 0 else plx.WORK_TRACK) for i in range(64)]
+    sizes = [c.width * c.height for c in cams_np]
+    offs = np.cumsum([0] + sizes)
+    rows = int(offs[-1])
+    o = plx.opts_from_dict(dict(step=0.5 * float(sc.grid.h[0]), lambda_d=1.0, depth_is_z=True))
+    cams = plx.CameraSet(cams_np)
+    rgb_t = torch.from_numpy(rgb_np).cuda()
+    depth_t = torch.from_numpy(depth_np).cuda()
+    mi = [i for i, (_, m) in enumerate(work) if m == plx.WORK_MAP]
+    ti = [i for i, (_, m) in enumerate(work) if m == plx.WORK_TRACK]
+    mrows = torch.from_numpy(np.concatenate([np.arange(offs[i], offs[i + 1]) for i in mi])).cuda()
+    map_cams = plx.CameraSet([cams_np[i] for i in mi])
+    trk_cams = plx.CameraSet([cams_np[i] for i in ti])
+    rgb_m, depth_m = rgb_t[mrows].contiguous(), depth_t[mrows].contiguous()
+    trk = [(rgb_t[offs[i]:offs[i + 1]], depth_t[offs[i]:offs[i + 1]]) for i in ti]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"room512mix: 512^3 grid, {sc.grid.n_alloc} allocated, 64 frames drawn "
+                       f"from 320x240/640x480/848x480/1200x680 ({rows} rays), 32 mapped "
+                       "(forward + adjoint) and 32 tracked (pose Jacobian) in one launch",
+           "unit": "rays/s"}
+
+    def timed(fn, K, W):
+        for _ in range(W):
+            fn()
+        barrier()
+        ev = []
+        for _ in range(K):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            ev.append((a, b))
+        barrier()
+        return sum(x.elapsed_time(y) for x, y in ev) / K
+
+    for storage in ("bf16", "f32"):
+        grid = plx.Grid.from_scene(sc.grid, storage)
+        grad = torch.zeros(grid.n_alloc, plx.GRAD_STRIDE, device="cuda")
+        mloss = torch.empty(2, device="cuda", dtype=torch.float64)
+        bo = (torch.empty(32, 6, 6, device="cuda", dtype=torch.float64),
+              torch.empty(32, 6, device="cuda", dtype=torch.float64),
+              torch.empty(32, 2, device="cuda", dtype=torch.float64))
+
+        def batch():
+            grad.zero_()
+            plx.render_batch(grid, cams, work, o, rgb_t, depth_t, grad=grad, map_loss=mloss, out=bo)
+
+        fw = plx.render_forward(grid, map_cams, o)
+        po = (torch.empty(6, 6, device="cuda", dtype=torch.float64),
+              torch.empty(6, device="cuda", dtype=torch.float64),
+              torch.empty(2, device="cuda", dtype=torch.float64))
+
+        def separate():
+            grad.zero_()
+            plx.render_forward(grid, map_cams, o, out=fw)
+            plx.render_backward_grid(grid, map_cams, o, rgb_m, depth_m, fw["rgb"], fw["depth"],
+                                     grad=grad, loss=mloss)
+            for k, (r_, d_) in enumerate(trk):
+                plx.render_backward_pose(grid, trk_cams, k, o, r_, d_, out=po)
+
+        ms_b = timed(batch, max(2, args.steps // 2), args.warmup)
+        ms_s = timed(separate, max(2, args.steps // 2), args.warmup)
+        out[storage] = {"value": rows / (ms_b / 1e3), "ms_per_batch": ms_b,
+                        "separate_calls": {"value": rows / (ms_s / 1e3), "ms": ms_s,
+                                           "launches": 3 + 32}}
+        grid.close()
+    out["value"] = out["bf16"]["value"]
     return out
 
 
@@ -499,6 +585,7 @@ def main():
     ap.add_argument("--tracking-iters", type=int, default=100)
     ap.add_argument("--no-tracking", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-rays-per-step", type=int, default=512)
     args = ap.parse_args()

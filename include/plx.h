@@ -264,6 +264,40 @@ plx_status plx_pose_step(const double *JtWJ, const double *JtWr, double damping,
                          double *pose, double *xi_out, int32_t *status,
                          void *stream);
 
+/* Kinds of work in a batch. */
+typedef enum { PLX_WORK_MAP = 0, PLX_WORK_TRACK = 1 } plx_work_mode;
+
+typedef struct {
+  int32_t cam;  /* camera index in plx_cameras (a camera may appear more than once) */
+  int32_t mode; /* plx_work_mode */
+} plx_work;
+
+/* Sec. 5.2 + Sec. 5.3 in one persistent launch: frames of any sizes, some to
+ * map (forward, loss and adjoint to the grid, as plx_render_forward followed
+ * by plx_render_backward_grid) and some to track (as
+ * plx_render_backward_pose), processed by one kernel that pulls 32-ray tiles
+ * from a global counter, mapping tiles first.
+ *   work         HOST [n_work], 1 <= n_work <= PLX_MAX_CAMERAS
+ *   rgb_target   DEVICE float [rows][3], depth_target DEVICE float [rows]:
+ *                every pixel of every item, item after item in the order of
+ *                `work`, row-major inside an item
+ *   grad         DEVICE float [n_alloc][PLX_GRAD_STRIDE], 16-byte aligned:
+ *                ADDS dL/d(value) of the mapping loss over all mapping items
+ *                (one M over all of them); may be NULL without mapping items
+ *   map_loss     DEVICE double [2] or NULL: overwritten with (L, M)
+ *   JtWJ, JtWr, track_loss  DEVICE double [n_track][36], [n_track][6],
+ *                [n_track][2], n_track = number of tracking items, in their
+ *                order in `work`; overwritten; may be NULL without tracking
+ *                items. Each item's sums are FP64; the order in which tiles
+ *                add into them varies between runs (last-bit differences).
+ * Errors: PLX_EINVAL, PLX_ECUDA. */
+plx_status plx_render_batch(const plx_grid *grid, const plx_cameras *cams,
+                            const plx_work *work, int32_t n_work,
+                            const plx_render_opts *opts, const float *rgb_target,
+                            const float *depth_target, float *grad,
+                            double *map_loss, double *JtWJ, double *JtWr,
+                            double *track_loss, void *stream);
+
 /* Reads and clears the grid's device error word (synchronises `stream`).
  * Returns PLX_EDEVICE_CHECK if a device-side check failed since the last
  * call. */

@@ -23,6 +23,11 @@ void launch_backward_pose(int store, const Common& P, const float* rgb_t, const 
 void launch_pose_step(const double* H, const double* b, double damping, double* pose,
                       double* xi_out, int32_t* status, cudaStream_t s);
 int pose_kernel_blocks_per_sm(int store);
+int batch_kernel_blocks_per_sm(int store);
+void launch_batch(int store, const Common& P, int n_track, const float* rgb_t,
+                  const float* depth_t, float* grad, double* map_loss, double* JtWJ, double* JtWr,
+                  double* track_loss, unsigned long long* Mmap, double* track_acc,
+                  unsigned long long* counter, int blocks, int num_sms, cudaStream_t s);
 }  // namespace plx
 
 using namespace plx;
@@ -32,8 +37,11 @@ struct Workspace {
   int32_t err;                    // device error word
   unsigned int retire;            // pose-reduction retirement counter
   unsigned long long M;           // valid-ray count of the last backward call
-  unsigned long long pad[5];
-  // followed by double partials[max_blocks][32]
+  unsigned long long tile_counter; // batch: next tile to hand out
+  unsigned long long M_map;       // batch: valid rays of the mapping items
+  unsigned long long pad[3];
+  // followed by double partials[max_blocks][32], then the batch's per-item
+  // tracking accumulators double[PLX_MAX_CAMERAS][32]
 };
 
 struct plx_grid {
@@ -45,6 +53,7 @@ struct plx_grid {
   int rec_bytes = 0;
   char* ws = nullptr;
   int max_pose_blocks = 0;
+  int batch_blocks[4] = {0, 0, 0, 0};
   int num_sms = 0;
   int device = 0;
   double inv_h[3];
@@ -226,7 +235,9 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
     bps = b > bps ? b : bps;
   }
   g->max_pose_blocks = g->num_sms * bps;
-  const size_t ws_bytes = sizeof(Workspace) + (size_t)g->max_pose_blocks * 32 * sizeof(double);
+  for (int st = 0; st < 4; ++st) g->batch_blocks[st] = g->num_sms * batch_kernel_blocks_per_sm(st);
+  const size_t ws_bytes = sizeof(Workspace) +
+                          ((size_t)g->max_pose_blocks + PLX_MAX_CAMERAS) * 32 * sizeof(double);
   e = cudaMalloc(&g->links, (size_t)n_links * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&g->rec, (size_t)(desc->n_alloc > 0 ? desc->n_alloc : 1) * g->rec_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&g->ws, ws_bytes);
@@ -373,6 +384,7 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
     cp.cy = split_ff(in.cy);
     cp.width = in.width;
     cp.height = in.height;
+    cp.pose_idx = c;
     cp.supers_x = (in.width + kTileW * kSuperW - 1) / (kTileW * kSuperW);
     const int supers_y = (in.height + kTileH * kSuperH - 1) / (kTileH * kSuperH);
     const bool use = fixed_cam < 0 || fixed_cam == c;
@@ -471,6 +483,72 @@ plx_status plx_pose_step(const double* JtWJ, const double* JtWr, double damping,
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ batched work
+extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cams,
+                                       const plx_work* work, int32_t n_work,
+                                       const plx_render_opts* opts, const float* rgb_target,
+                                       const float* depth_target, float* grad, double* map_loss,
+                                       double* JtWJ, double* JtWr, double* track_loss,
+                                       void* stream) {
+  const char* what = "render_batch";
+  if (!work || n_work < 1 || n_work > PLX_MAX_CAMERAS)
+    return fail(PLX_EINVAL, "%s: n_work %d out of [1, %d]", what, n_work, PLX_MAX_CAMERAS);
+  plx_rays dense;
+  dense.n_rays = 0;
+  dense.cam_id = nullptr;
+  dense.pixel = nullptr;
+  Common P;
+  plx_status st = build_common(what, g, cams, &dense, opts, -1, P);
+  if (st != PLX_OK) return st;
+  const CamTable base = P.ct;
+  int n_map = 0, n_track = 0;
+  int64_t rows = 0;
+  int64_t row_of[PLX_MAX_CAMERAS];
+  for (int i = 0; i < n_work; ++i) {
+    if (work[i].cam < 0 || work[i].cam >= cams->n_cams)
+      return fail(PLX_EINVAL, "%s: work[%d].cam = %d out of range", what, i, work[i].cam);
+    if (work[i].mode != PLX_WORK_MAP && work[i].mode != PLX_WORK_TRACK)
+      return fail(PLX_EINVAL, "%s: work[%d].mode = %d", what, i, work[i].mode);
+    row_of[i] = rows;
+    rows += (int64_t)base.cam[work[i].cam].width * base.cam[work[i].cam].height;
+    (work[i].mode == PLX_WORK_MAP ? n_map : n_track) += 1;
+  }
+  if (n_map > 0 && (!grad || reinterpret_cast<uintptr_t>(grad) % 16 != 0))
+    return fail(PLX_EINVAL, "%s: mapping work needs a 16-byte aligned grad", what);
+  if (n_track > 0 && (!JtWJ || !JtWr || !track_loss))
+    return fail(PLX_EINVAL, "%s: tracking work needs JtWJ, JtWr and track_loss", what);
+  if (rows > 0 && (!rgb_target || !depth_target))
+    return fail(PLX_EINVAL, "%s: null target", what);
+  // the tile space: mapping items first, then tracking items, each in work order
+  int e = 0, slot = 0;
+  int64_t tiles = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i < n_work; ++i) {
+      if ((work[i].mode == PLX_WORK_TRACK) != (pass == 1)) continue;
+      CamParam cp = base.cam[work[i].cam];
+      const int supers_y = (cp.height + kTileH * kSuperH - 1) / (kTileH * kSuperH);
+      cp.pose_idx = work[i].cam;
+      cp.mode = work[i].mode;
+      cp.slot = pass == 1 ? slot++ : -1;
+      cp.ray_off = row_of[i];
+      cp.tile_off = tiles;
+      tiles += (int64_t)cp.supers_x * supers_y * kSuperW * kSuperH;
+      P.ct.cam[e++] = cp;
+    }
+  }
+  P.ct.n_cams = n_work;
+  P.ct.dense = 1;
+  P.ct.n_rays = rows;
+  P.ct.n_tiles = tiles;
+  Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
+  double* track_acc =
+      reinterpret_cast<double*>(g->ws + sizeof(Workspace)) + (size_t)g->max_pose_blocks * 32;
+  launch_batch(g->desc.storage, P, n_track, rgb_target, depth_target, grad, map_loss, JtWJ, JtWr,
+               track_loss, &ws->M_map, track_acc, &ws->tile_counter, g->batch_blocks[g->desc.storage],
+               g->num_sms, (cudaStream_t)stream);
+  return launch_check(what);
+}
 
 // -------------------------------------------------- allocation-free variant
 // plx_render_backward_pose_noalloc keeps its scratch (error word, retirement

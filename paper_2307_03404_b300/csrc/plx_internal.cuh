@@ -36,7 +36,9 @@ struct CamParam {
   int64_t ray_off;                // dense mode: index of the camera's ray 0
   int64_t tile_off;               // dense mode: index of the camera's tile 0
   int32_t supers_x;               // 16x16 supertiles per row
-  int32_t pad;
+  int32_t pose_idx;               // row of the poses array (a batch may name a camera twice)
+  int32_t mode;                   // batch work: PLX_WORK_MAP or PLX_WORK_TRACK
+  int32_t slot;                   // batch work: index among the tracking items
 };
 
 struct CamTable {
@@ -224,9 +226,10 @@ __device__ __forceinline__ void setup_ray(const Common& P, const RayId& id, RayF
   // the pose [R | o] as float pairs: converted once per warp when the warp
   // shares a camera (always in dense mode), else by each lane
   float Ph[12], Pl[12];
-  const int cam0 = __shfl_sync(0xffffffffu, id.cam, 0);
-  if (__all_sync(0xffffffffu, id.cam == cam0)) {
-    const double v = __ldg(P.poses + 12 * cam0 + (lane < 12 ? lane : 0));
+  const int pidx = P.ct.cam[id.cam].pose_idx;
+  const int p0 = __shfl_sync(0xffffffffu, pidx, 0);
+  if (__all_sync(0xffffffffu, pidx == p0)) {
+    const double v = __ldg(P.poses + 12 * p0 + (lane < 12 ? lane : 0));
     const float vh = (float)v, vl = (float)(v - (double)vh);
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
@@ -236,7 +239,7 @@ __device__ __forceinline__ void setup_ray(const Common& P, const RayId& id, RayF
   } else {
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
-      const double v = __ldg(P.poses + 12 * id.cam + j);
+      const double v = __ldg(P.poses + 12 * pidx + j);
       Ph[j] = (float)v;
       Pl[j] = (float)(v - (double)Ph[j]);
     }

@@ -1,0 +1,219 @@
+// Ray-march loops shared by the forward, adjoint and batched kernels.
+#pragma once
+
+#include "plx_internal.cuh"
+
+namespace plx {
+
+template <int STORE, bool COUNT>
+__device__ __forceinline__ void march_forward(const Common& P, const RayF& r, const float Y[9],
+                                              float C[3], float& D, float& T, int& n_all,
+                                              int& n_occ) {
+  const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
+  int cx = -1, cy = -1, cz = -1;
+  bool empty = true;
+  int32_t l[8];
+  float cs[8], cc[8][3];
+  C[0] = C[1] = C[2] = 0.f;
+  D = 0.f;
+  T = 1.f;
+  n_all = r.n;
+  for (int k = 0; k < r.n; ++k) {
+    const float kf = (float)k;
+    int ix, iy, iz;
+    float fx, fy, fz;
+    sample_axis(r.bh[0], r.bl[0], r.sh[0], r.sl[0], kf, rm2x, ix, fx);
+    sample_axis(r.bh[1], r.bl[1], r.sh[1], r.sl[1], kf, rm2y, iy, fy);
+    sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
+    if (ix != cx || iy != cy || iz != cz) {
+      cx = ix; cy = iy; cz = iz;
+      if (block_empty(P.g, ix, iy, iz)) {
+        empty = true;
+        k = block_exit(r, ix, iy, iz, k) - 1;
+        continue;
+      }
+      empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
+    }
+    if (COUNT) n_occ += empty ? 0 : 1;
+    if (empty) continue;
+    float w[8];
+    corner_weights(fx, fy, fz, w);
+    float sig = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sig = fmaf(w[c], cs[c], sig);
+    if (!(sig > 0.f)) continue;
+    float col[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float a = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) a = fmaf(w[c], cc[c][ch], a);
+      float dact;
+      col[ch] = activate(a, P.o.color_act, dact);
+    }
+    float alpha, keep;
+    alpha_of(sig * r.dt, alpha, keep);
+    const float wgt = T * alpha;
+    const float t = fmaf(kf, r.dt, r.t0);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(wgt, col[ch], C[ch]);
+    D = fmaf(wgt, t, D);
+    T *= keep;
+    if (T < P.o.stop_T) {
+      n_all = k + 1;
+      break;
+    }
+  }
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], C[ch]);
+}
+
+// ------------------------------------------------------------------ adjoint
+__device__ __forceinline__ void flush_corner(float* __restrict__ grad, int32_t link, float gs,
+                                             const float gc[3], const float Y[9]) {
+  if (link < 0) return;
+  float v[28];
+  v[0] = gs;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[1 + 9 * ch + k] = gc[ch] * Y[k];
+  float4* dst = reinterpret_cast<float4*>(grad + (int64_t)link * PLX_GRAD_STRIDE);
+#pragma unroll
+  for (int j = 0; j < 7; ++j)
+    atomicAdd(dst + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+}
+
+__device__ __forceinline__ void clear_corner(float& gs, float gc[3]) {
+  gs = 0.f;
+  gc[0] = gc[1] = gc[2] = 0.f;
+}
+
+__device__ __forceinline__ void flush_cell(float* __restrict__ grad, const int32_t l[8],
+                                           float gs[8], float gc[8][3], const float Y[9]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    flush_corner(grad, l[c], gs[c], gc[c], Y);
+    clear_corner(gs[c], gc[c]);
+  }
+}
+
+// The ray steps into the face-adjacent cell along corner bit B (1 = x, 2 = y,
+// 4 = z), forward if POS. The 4 corners on the shared face are the same
+// vertices in both cells: their sums stay in registers and move to their slot
+// in the new cell; only the 4 corners left behind are flushed. This cuts the
+// adjoint's atomics by up to half.
+template <int B, bool POS>
+__device__ __forceinline__ void carry_cell(float* __restrict__ grad, const int32_t l[8],
+                                           float gs[8], float gc[8][3], const float Y[9]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (POS == ((c & B) == 0)) flush_corner(grad, l[c], gs[c], gc[c], Y);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (POS == ((c & B) == 0)) {  // new corner c takes old corner c ^ B
+      gs[c] = gs[c ^ B];
+      gc[c][0] = gc[c ^ B][0];
+      gc[c][1] = gc[c ^ B][1];
+      gc[c][2] = gc[c ^ B][2];
+      clear_corner(gs[c ^ B], gc[c ^ B]);
+    }
+  }
+}
+
+template <int STORE>
+__device__ __forceinline__ void march_backward(const Common& P, const RayF& r, const float Y[9],
+                                               const float Cf[3], float Df, const float gC[3],
+                                               float gD, float* __restrict__ grad) {
+  const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
+  int cx = -1, cy = -1, cz = -1;
+  bool empty = true, dirty = false;
+  int32_t l[8];
+  __shared__ float cache[32 * kBlock];  // corner cache in shared memory: frees 32 registers
+  float* sc = cache + threadIdx.x;
+  float gs[8], gc[8][3];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) clear_corner(gs[c], gc[c]);
+  float S[3] = {0.f, 0.f, 0.f}, SD = 0.f, T = 1.f;
+  const float dt = r.dt;
+  for (int k = 0; k < r.n; ++k) {
+    const float kf = (float)k;
+    int ix, iy, iz;
+    float fx, fy, fz;
+    sample_axis(r.bh[0], r.bl[0], r.sh[0], r.sl[0], kf, rm2x, ix, fx);
+    sample_axis(r.bh[1], r.bl[1], r.sh[1], r.sl[1], kf, rm2y, iy, fy);
+    sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
+    if (ix != cx || iy != cy || iz != cz) {
+      const bool skip = block_empty(P.g, ix, iy, iz);
+      if (dirty) {
+        const int dx = ix - cx, dy = iy - cy, dz = iz - cz;
+        int step = -1;  // face-adjacent step: 0/1 = +x/-x, 2/3 = +y/-y, 4/5 = +z/-z
+        if (!skip) {
+          if (dy == 0 && dz == 0) step = dx == 1 ? 0 : (dx == -1 ? 1 : -1);
+          else if (dx == 0 && dz == 0) step = dy == 1 ? 2 : (dy == -1 ? 3 : -1);
+          else if (dx == 0 && dy == 0) step = dz == 1 ? 4 : (dz == -1 ? 5 : -1);
+        }
+        switch (step) {
+          case 0: carry_cell<1, true>(grad, l, gs, gc, Y); break;
+          case 1: carry_cell<1, false>(grad, l, gs, gc, Y); break;
+          case 2: carry_cell<2, true>(grad, l, gs, gc, Y); break;
+          case 3: carry_cell<2, false>(grad, l, gs, gc, Y); break;
+          case 4: carry_cell<4, true>(grad, l, gs, gc, Y); break;
+          case 5: carry_cell<4, false>(grad, l, gs, gc, Y); break;
+          default: flush_cell(grad, l, gs, gc, Y); break;
+        }
+        dirty = step >= 0;  // carried sums still have to reach memory
+      }
+      cx = ix; cy = iy; cz = iz;
+      if (skip) {
+        empty = true;
+        k = block_exit(r, ix, iy, iz, k) - 1;
+        continue;
+      }
+      empty = load_cell_smem<STORE>(P.g, ix, iy, iz, Y, l, sc);
+    }
+    if (empty) continue;
+    float w[8];
+    corner_weights(fx, fy, fz, w);
+    float sig = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sig = fmaf(w[c], sc[(4 * c) * kBlock], sig);
+    if (!(sig > 0.f)) continue;
+    float col[3], dact[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float a = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) a = fmaf(w[c], sc[(4 * c + 1 + ch) * kBlock], a);
+      col[ch] = activate(a, P.o.color_act, dact[ch]);
+    }
+    float alpha, keep;
+    alpha_of(sig * dt, alpha, keep);
+    const float wgt = T * alpha;
+    const float Tn = T * keep;
+    const float t = fmaf(kf, dt, r.t0);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) S[ch] = fmaf(wgt, col[ch], S[ch]);
+    SD = fmaf(wgt, t, SD);
+    // Eq. 9 and Eq. 10
+    float dsig = gD * dt * (t * Tn - Df + SD);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) dsig = fmaf(gC[ch] * dt, col[ch] * Tn - Cf[ch] + S[ch], dsig);
+    // Eq. 8 through the colour activation
+    float dch[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) dch[ch] = gC[ch] * wgt * dact[ch];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      gs[c] = fmaf(w[c], dsig, gs[c]);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) gc[c][ch] = fmaf(w[c], dch[ch], gc[c][ch]);
+    }
+    dirty = true;
+    T = Tn;
+    if (T < P.o.stop_T) break;
+  }
+  if (dirty) flush_cell(grad, l, gs, gc, Y);
+}
+
+}  // namespace plx

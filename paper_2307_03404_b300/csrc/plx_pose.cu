@@ -19,143 +19,9 @@
 // value L; from there everything is FP64: each lane keeps one FP64
 // accumulator across the rays it visits, and blocks write FP64 partials that
 // the last block to finish sums in a fixed order. The result is deterministic.
-#include "plx_internal.cuh"
+#include "plx_pose_march.cuh"
 
 namespace plx {
-
-// local gradient of the trilinear interpolant of corner values V (unit cell)
-__device__ __forceinline__ void grad_local(const float V[8], float x, float y, float z,
-                                           float g[3]) {
-  const float gx = 1.f - x, gy = 1.f - y, gz = 1.f - z;
-  g[0] = gy * gz * (V[1] - V[0]) + y * gz * (V[3] - V[2]) + gy * z * (V[5] - V[4]) +
-         y * z * (V[7] - V[6]);
-  g[1] = gx * gz * (V[2] - V[0]) + x * gz * (V[3] - V[1]) + gx * z * (V[6] - V[4]) +
-         x * z * (V[7] - V[5]);
-  g[2] = gx * gy * (V[4] - V[0]) + x * gy * (V[5] - V[1]) + gx * y * (V[6] - V[2]) +
-         x * y * (V[7] - V[3]);
-}
-
-struct PoseAcc {
-  float Po[4][3], Pd[4][3];  // per output X in (R, G, B, D)
-  float Qo[3], Qd[3];
-};
-
-template <int STORE>
-__device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const float Y[9],
-                                           float C[3], float& D, float& T, PoseAcc& A) {
-  const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
-  const float ihx = (float)P.g.inv_h[0], ihy = (float)P.g.inv_h[1], ihz = (float)P.g.inv_h[2];
-  int cx = -1, cy = -1, cz = -1;
-  bool empty = true;
-  int32_t l[8];
-  float cs[8], cc[8][3];
-  float S[3] = {0.f, 0.f, 0.f}, SD = 0.f;
-  T = 1.f;
-  const float dt = r.dt;
-  for (int k = 0; k < r.n; ++k) {
-    const float kf = (float)k;
-    int ix, iy, iz;
-    float fx, fy, fz;
-    sample_axis(r.bh[0], r.bl[0], r.sh[0], r.sl[0], kf, rm2x, ix, fx);
-    sample_axis(r.bh[1], r.bl[1], r.sh[1], r.sl[1], kf, rm2y, iy, fy);
-    sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
-    if (ix != cx || iy != cy || iz != cz) {
-      cx = ix; cy = iy; cz = iz;
-      if (block_empty(P.g, ix, iy, iz)) {
-        empty = true;
-        k = block_exit(r, ix, iy, iz, k) - 1;
-        continue;
-      }
-      empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
-    }
-    if (empty) continue;
-    float w[8];
-    corner_weights(fx, fy, fz, w);
-    float sig = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) sig = fmaf(w[c], cs[c], sig);
-    if (!(sig > 0.f)) continue;
-    float gsig[3];
-    grad_local(cs, fx, fy, fz, gsig);
-    gsig[0] *= ihx; gsig[1] *= ihy; gsig[2] *= ihz;
-    float alpha, keep;
-    alpha_of(sig * dt, alpha, keep);
-    const float wgt = T * alpha;
-    const float Tn = T * keep;
-    const float t = fmaf(kf, dt, r.t0);
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float V[8];
-      float a = 0.f;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) { V[c] = cc[c][ch]; a = fmaf(w[c], V[c], a); }
-      float dact;
-      const float col = activate(a, P.o.color_act, dact);
-      float gch[3];
-      grad_local(V, fx, fy, fz, gch);
-      S[ch] = fmaf(wgt, col, S[ch]);
-      const float cs_coef = dt * (col * Tn + S[ch]);
-      const float cc_coef = wgt * dact;
-      const float u0 = cs_coef * gsig[0] + cc_coef * gch[0] * ihx;
-      const float u1 = cs_coef * gsig[1] + cc_coef * gch[1] * ihy;
-      const float u2 = cs_coef * gsig[2] + cc_coef * gch[2] * ihz;
-      A.Po[ch][0] += u0; A.Po[ch][1] += u1; A.Po[ch][2] += u2;
-      A.Pd[ch][0] = fmaf(t, u0, A.Pd[ch][0]);
-      A.Pd[ch][1] = fmaf(t, u1, A.Pd[ch][1]);
-      A.Pd[ch][2] = fmaf(t, u2, A.Pd[ch][2]);
-    }
-    SD = fmaf(wgt, t, SD);
-    const float dcoef = dt * (t * Tn + SD);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float ud = dcoef * gsig[a];
-      A.Po[3][a] += ud;
-      A.Pd[3][a] = fmaf(t, ud, A.Pd[3][a]);
-      const float q = dt * gsig[a];
-      A.Qo[a] += q;
-      A.Qd[a] = fmaf(t, q, A.Qd[a]);
-    }
-    T = Tn;
-    if (T < P.o.stop_T) break;
-  }
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], S[ch]);
-  D = SD;
-}
-
-// Per-ray values reduced: 21 of H (index below), 6 of b at 21..26, the loss at
-// 27 and the valid-ray count at 28. Value index of H_ij (i <= j):
-__host__ __device__ constexpr int hidx(int i, int j) { return i * 6 - i * (i - 1) / 2 + (j - i); }
-
-// Warp reduce-scatter of v[0..31]: lane L returns the sum over the warp of
-// v[L]. Sums are carried as float-float pairs (about 44 significant bits), so
-// the FP32 pipes do the work and the FP64 pipe, slow on this part, is used
-// once per lane at the end.
-__device__ __forceinline__ double warp_reduce_scatter(const float v[32], int lane) {
-  ff a[16];
-  {
-    const bool up = lane & 16;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float send = up ? v[i] : v[i + 16];
-      const float keep = up ? v[i + 16] : v[i];
-      a[i] = two_sum(keep, __shfl_xor_sync(0xffffffffu, send, 16));
-    }
-  }
-#pragma unroll
-  for (int off = 8; off >= 1; off >>= 1) {
-    const bool up = lane & off;
-#pragma unroll
-    for (int i = 0; i < off; ++i) {
-      const ff send = up ? a[i] : a[i + off];
-      const ff keep = up ? a[i + off] : a[i];
-      const ff recv = ffv(__shfl_xor_sync(0xffffffffu, send.h, off),
-                          __shfl_xor_sync(0xffffffffu, send.l, off));
-      a[i] = ff_add(keep, recv);
-    }
-  }
-  return (double)a[0].h + (double)a[0].l;
-}
 
 template <int STORE>
 __global__ void __launch_bounds__(kBlock, PLX_POSE_MIN_BLOCKS)
@@ -166,7 +32,6 @@ k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_
   __shared__ double red[kWarpsPerBlock][32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float lam = P.o.lambda_d;
   double acc = 0.0;
   const int64_t warps_total = (int64_t)gridDim.x * kWarpsPerBlock;
   for (int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + warp; tile < P.ct.n_tiles;
@@ -179,54 +44,7 @@ k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_
     setup_ray(P, id, r, lane);
     float dz = 0.f;
     if (id.valid) dz = __ldg(depth_t + id.out);
-    if (id.valid && depth_valid(dz)) {
-      float Y[9];
-      sh_basis(r.dir, Y);
-      PoseAcc A;
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) A.Po[x][a] = A.Pd[x][a] = 0.f;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) A.Qo[a] = A.Qd[a] = 0.f;
-      float C[3], D, T;
-      march_pose<STORE>(P, r, Y, C, D, T, A);
-      const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
-      float res[4], J[4][6];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        const float X = x < 3 ? C[x] : D;
-        res[x] = X - (x < 3 ? __ldg(rgb_t + 3 * id.out + x) : Dt);
-        float jo[3], jd[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          jo[a] = A.Po[x][a] - X * A.Qo[a];
-          jd[a] = A.Pd[x][a] - X * A.Qd[a];
-        }
-        const float* o = r.org;
-        const float* d = r.dir;
-        J[x][0] = jo[0]; J[x][1] = jo[1]; J[x][2] = jo[2];
-        J[x][3] = (o[1] * jo[2] - o[2] * jo[1]) + (d[1] * jd[2] - d[2] * jd[1]);
-        J[x][4] = (o[2] * jo[0] - o[0] * jo[2]) + (d[2] * jd[0] - d[0] * jd[2]);
-        J[x][5] = (o[0] * jo[1] - o[1] * jo[0]) + (d[0] * jd[1] - d[1] * jd[0]);
-      }
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-#pragma unroll
-        for (int j = i; j < 6; ++j) {
-          float h = J[3][i] * J[3][j] * lam;
-#pragma unroll
-          for (int x = 0; x < 3; ++x) h = fmaf(J[x][i], J[x][j], h);
-          v[hidx(i, j)] = h;
-        }
-        float bb = J[3][i] * res[3] * lam;
-#pragma unroll
-        for (int x = 0; x < 3; ++x) bb = fmaf(J[x][i], res[x], bb);
-        v[21 + i] = bb;
-      }
-      v[27] = res[0] * res[0] + res[1] * res[1] + res[2] * res[2] + lam * res[3] * res[3];
-      v[28] = 1.f;
-    }
+    if (id.valid && depth_valid(dz)) pose_ray_values<STORE>(P, r, rgb_t + 3 * id.out, dz, v);
     acc += warp_reduce_scatter(v, lane);
   }
   red[warp][lane] = acc;

@@ -55,6 +55,13 @@ class Rays(C.Structure):
     _fields_ = [("n_rays", C.c_int64), ("cam_id", C.c_void_p), ("pixel", C.c_void_p)]
 
 
+class Work(C.Structure):
+    _fields_ = [("cam", C.c_int32), ("mode", C.c_int32)]
+
+
+WORK_MAP, WORK_TRACK = 0, 1
+
+
 class RenderOpts(C.Structure):
     _fields_ = [("step", C.c_double), ("near_t", C.c_double), ("stop_T", C.c_double),
                 ("bg", C.c_float * 3), ("lambda_d", C.c_float), ("max_samples", C.c_int32),
@@ -64,7 +71,7 @@ class RenderOpts(C.Structure):
 SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload",
            "plx_grid_download", "plx_grid_info", "plx_grid_destroy", "plx_render_forward",
            "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
-           "plx_grid_check", "plx_render_backward_pose_noalloc"]
+           "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch"]
 
 
 def _load():
@@ -89,6 +96,8 @@ def _load():
         "plx_render_backward_pose": [P, C.POINTER(Cameras), I32, C.POINTER(Rays),
                                      C.POINTER(RenderOpts), P, P, P, P, P, P],
         "plx_pose_step": [P, P, D, P, P, P, P],
+        "plx_render_batch": [P, C.POINTER(Cameras), C.POINTER(Work), I32, C.POINTER(RenderOpts),
+                             P, P, P, P, P, P, P, P],
         "plx_render_backward_pose_noalloc": [C.POINTER(GridDesc), P, P, C.POINTER(Cameras), I32,
                                              C.POINTER(Rays), C.POINTER(RenderOpts), P, P, P, P,
                                              P, P],
@@ -312,3 +321,32 @@ def pose_step(JtWJ, JtWr, pose, damping=0.0, xi_out=None, status=None, stream=No
     """plx_pose_step: pose (device float64 [12] view) <- exp(xi^) pose."""
     _check(_lib.plx_pose_step(_ptr(JtWJ), _ptr(JtWr), float(damping), _ptr(pose), _ptr(xi_out),
                               _ptr(status), _stream(stream)))
+
+
+def render_batch(grid: Grid, cams: CameraSet, work, opts, rgb_target, depth_target, grad=None,
+                 map_loss=None, out=None, stream=None):
+    """plx_render_batch. ``work`` = [(cam, WORK_MAP | WORK_TRACK), ...]; targets
+    hold every pixel of every item in that order. Returns (grad [n_alloc, 32] or
+    None, map_loss [2] or None, JtWJ [n_track, 6, 6], JtWr [n_track, 6],
+    track_loss [n_track, 2])."""
+    work = list(work)
+    arr = (Work * len(work))()
+    for i, (c, m) in enumerate(work):
+        arr[i].cam, arr[i].mode = int(c), int(m)
+    n_track = sum(1 for _, m in work if m == WORK_TRACK)
+    n_map = len(work) - n_track
+    if grad is None and n_map:
+        grad = torch.zeros(grid.n_alloc, GRAD_STRIDE, device="cuda")
+    if map_loss is None and n_map:
+        map_loss = torch.empty(2, device="cuda", dtype=torch.float64)
+    if out is None:
+        k = max(n_track, 1)
+        out = (torch.empty(k, 6, 6, device="cuda", dtype=torch.float64),
+               torch.empty(k, 6, device="cuda", dtype=torch.float64),
+               torch.empty(k, 2, device="cuda", dtype=torch.float64))
+    cs = cams.struct()
+    _check(_lib.plx_render_batch(grid.handle, C.byref(cs), arr, len(work), C.byref(opts),
+                                 _ptr(rgb_target), _ptr(depth_target), _ptr(grad),
+                                 _ptr(map_loss), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
+                                 _stream(stream)))
+    return grad, map_loss, out[0][:n_track], out[1][:n_track], out[2][:n_track]
