@@ -264,6 +264,44 @@ plx_status plx_pose_step(const double *JtWJ, const double *JtWr, double damping,
                          double *pose, double *xi_out, int32_t *status,
                          void *stream);
 
+/* Sec. 5.4 (RMSProp for the mapping). One RMSProp step on every stored grid
+ * value, in place, from the gradient left by plx_render_backward_grid:
+ *   v <- alpha v + (1 - alpha) g^2,  value <- value - lr g / (sqrt(v) + eps)
+ * computed in FP32 and stored in the grid's storage format (16-bit formats
+ * round to nearest even).
+ *   grad   DEVICE float [n_alloc][PLX_GRAD_STRIDE], slots 0..27; set to zero
+ *          by the call when zero_grad != 0 (ready for the next adjoint)
+ *   state  DEVICE float [n_alloc][PLX_GRAD_STRIDE]: the running v, zeroed by
+ *          the caller before the first step
+ * Asynchronous; graph-capturable. Errors: PLX_EINVAL. */
+plx_status plx_grid_rmsprop(plx_grid *grid, float *grad, float *state, float lr,
+                            float alpha, float eps, int32_t zero_grad,
+                            void *stream);
+
+/* Sec. 5.3-5.4 (tracking by random rays of the current image, Adam). One
+ * iteration on camera `cam`: n_rays pixels drawn from the frame with the
+ * counter-based generator SplitMix64 (Steele, Lea and Flood 2014; ray i of
+ * iteration t is pixel mix(seed + (t n_rays + i + 1) * 0x9E3779B97F4A7C15)
+ * mod (W H), pixels may repeat), their pose system as in
+ * plx_render_backward_pose (written to JtWJ, JtWr, loss), the loss gradient
+ * g = 2 JtWr with respect to a left perturbation, and an Adam step
+ *   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+ *   xi = -lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ *   pose <- exp(xi^) pose   (cams->poses row `cam`, in place).
+ *   rgb_target, depth_target  DEVICE, the whole frame: [W*H][3], [W*H]
+ *   state  DEVICE double [20]: m[0..5], v[6..11], t at [12] (iterations done,
+ *          also the generator counter), last xi at [13..18]; zeroed by the
+ *          caller before the first iteration.
+ * Asynchronous; graph-capturable (the counter lives on the device). */
+plx_status plx_track_adam_step(const plx_grid *grid, const plx_cameras *cams,
+                               int32_t cam, const plx_render_opts *opts,
+                               int32_t n_rays, uint64_t seed,
+                               const float *rgb_target,
+                               const float *depth_target, double *state,
+                               double lr, double beta1, double beta2,
+                               double eps, double *JtWJ, double *JtWr,
+                               double *loss, void *stream);
+
 /* Kinds of work in a batch. */
 typedef enum { PLX_WORK_MAP = 0, PLX_WORK_TRACK = 1 } plx_work_mode;
 

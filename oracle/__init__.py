@@ -274,3 +274,62 @@ def trilerp(V, x, y, z):
     g = np.zeros(3)
     _load().orc_trilerp(_ptr(V), C.c_double(x), C.c_double(y), C.c_double(z), _ptr(f), _ptr(g))
     return float(f[0]), g
+
+
+# ----------------------------------------------------------- optimisers
+# Sec. 5.4: RMSProp for the mapping, Adam for the tracking on rays drawn at
+# random from the current image. Plain formulas, FP64.
+
+def rmsprop(x, g, v, lr, alpha, eps):
+    """One RMSProp step: v <- alpha v + (1 - alpha) g^2, x <- x - lr g / (sqrt(v) + eps)."""
+    x, g, v = (np.asarray(a, np.float64) for a in (x, g, v))
+    v = alpha * v + (1.0 - alpha) * g * g
+    return x - lr * g / (np.sqrt(v) + eps), v
+
+
+def adam(g, m, v, t, lr, b1, b2, eps):
+    """One Adam step on a parameter vector; t counts from 1. Returns (step, m, v)."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return -lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+_GOLDEN_GAMMA = 0x9E3779B97F4A7C15
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(seed, k):
+    """SplitMix64 (Steele, Lea and Flood, 2014) as a counter-based generator:
+    value k of stream ``seed`` is mix(seed + (k + 1) * golden gamma)."""
+    z = (int(seed) + (int(k) + 1) * _GOLDEN_GAMMA) & _MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+    return z ^ (z >> 31)
+
+
+def random_pixels(seed, t, n, n_pixels):
+    """The n pixels of tracking iteration t: splitmix64(seed, t n + i) mod n_pixels."""
+    return np.array([splitmix64(seed, t * n + i) % n_pixels for i in range(n)], np.int32)
+
+
+def adam_track(grid, cam, opts, rgb_t, depth_t, n_rays, seed, iters, lr, b1=0.9, b2=0.999,
+               eps=1e-8):
+    """The paper's tracker: per iteration, n_rays random pixels of the frame,
+    the loss gradient 2 J^T W r with respect to a left perturbation (Eq. 12-14),
+    an Adam step xi and T <- exp(xi^) T. rgb_t / depth_t hold the whole frame.
+    Returns the final pose and the per-iteration losses."""
+    T = np.asarray(cam.T_wc, np.float64).reshape(3, 4)
+    m, v = np.zeros(6), np.zeros(6)
+    npx = int(cam.width) * int(cam.height)
+    losses = []
+    for t in range(iters):
+        pix = random_pixels(seed, t, n_rays, npx)
+        pj = pose_jacobian(grid, [cam.with_pose(T)], opts, np.asarray(rgb_t)[pix],
+                           np.asarray(depth_t)[pix], rays=(np.zeros(n_rays, np.int32), pix))
+        xi, m, v = adam(2.0 * pj.b, m, v, t + 1, lr, b1, b2, eps)
+        E = np.vstack([se3_exp(xi), [0, 0, 0, 1]])
+        T = (E @ np.vstack([T, [0, 0, 0, 1]]))[:3]
+        losses.append(pj.loss)
+    return T, losses

@@ -24,6 +24,10 @@ void launch_pose_step(const double* H, const double* b, double damping, double* 
                       double* xi_out, int32_t* status, cudaStream_t s);
 int pose_kernel_blocks_per_sm(int store);
 int batch_kernel_blocks_per_sm(int store);
+void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, float lr,
+                    float alpha, float eps, int zero_grad, int num_sms, cudaStream_t s);
+void launch_adam_pose(const double* JtWr, double* state, double* pose, double lr, double b1,
+                      double b2, double eps, cudaStream_t s);
 void launch_batch(int store, const Common& P, int n_track, const float* rgb_t,
                   const float* depth_t, float* grad, double* map_loss, double* JtWJ, double* JtWr,
                   double* track_loss, unsigned long long* Mmap, double* track_acc,
@@ -547,6 +551,59 @@ extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cam
   launch_batch(g->desc.storage, P, n_track, rgb_target, depth_target, grad, map_loss, JtWJ, JtWr,
                track_loss, &ws->M_map, track_acc, &ws->tile_counter, g->batch_blocks[g->desc.storage],
                g->num_sms, (cudaStream_t)stream);
+  return launch_check(what);
+}
+
+// ------------------------------------------------------------ optimisers
+extern "C" plx_status plx_grid_rmsprop(plx_grid* g, float* grad, float* state, float lr,
+                                       float alpha, float eps, int32_t zero_grad, void* stream) {
+  const char* what = "grid_rmsprop";
+  if (!g) return fail(PLX_EINVAL, "%s: null grid", what);
+  if (g->desc.n_alloc == 0) return PLX_OK;
+  if (!grad || !state || reinterpret_cast<uintptr_t>(grad) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(state) % 16 != 0)
+    return fail(PLX_EINVAL, "%s: grad and state must be non-null and 16-byte aligned", what);
+  if (!(lr >= 0.f) || !(alpha >= 0.f && alpha <= 1.f) || !(eps > 0.f))
+    return fail(PLX_EINVAL, "%s: need lr >= 0, 0 <= alpha <= 1, eps > 0", what);
+  launch_rmsprop(g->desc.storage, g->rec, grad, state, g->desc.n_alloc, lr, alpha, eps,
+                 zero_grad ? 1 : 0, g->num_sms, (cudaStream_t)stream);
+  return launch_check(what);
+}
+
+extern "C" plx_status plx_track_adam_step(const plx_grid* g, const plx_cameras* cams, int32_t cam,
+                                          const plx_render_opts* opts, int32_t n_rays,
+                                          uint64_t seed, const float* rgb_target,
+                                          const float* depth_target, double* state, double lr,
+                                          double beta1, double beta2, double eps, double* JtWJ,
+                                          double* JtWr, double* loss, void* stream) {
+  const char* what = "track_adam_step";
+  if (cam < 0) return fail(PLX_EINVAL, "%s: cam < 0", what);
+  if (n_rays < 1) return fail(PLX_EINVAL, "%s: n_rays must be >= 1", what);
+  if (!state || !JtWJ || !JtWr || !loss || !rgb_target || !depth_target)
+    return fail(PLX_EINVAL, "%s: null argument", what);
+  if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
+      !(eps > 0.0))
+    return fail(PLX_EINVAL, "%s: need lr >= 0, 0 <= beta < 1, eps > 0", what);
+  plx_rays dense;
+  dense.n_rays = 0;
+  dense.cam_id = nullptr;
+  dense.pixel = nullptr;
+  Common P;
+  plx_status st = build_common(what, g, cams, &dense, opts, cam, P);
+  if (st != PLX_OK) return st;
+  P.ct.dense = 0;
+  P.ct.n_rays = n_rays;
+  P.ct.n_tiles = ((int64_t)n_rays + 31) / 32;
+  P.rl.random = 1;
+  P.rl.seed = seed;
+  P.rl.iter = state + 12;
+  Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
+  double* partials = reinterpret_cast<double*>(g->ws + sizeof(Workspace));
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_backward_pose(g->desc.storage, P, rgb_target, depth_target, partials, &ws->retire, JtWJ,
+                       JtWr, loss, g->max_pose_blocks, s);
+  launch_adam_pose(JtWr, state, const_cast<double*>(cams->poses) + 12 * cam, lr, beta1, beta2, eps,
+                   s);
   return launch_check(what);
 }
 

@@ -53,7 +53,20 @@ struct RayList {
   const int32_t* cam_id;          // list mode, may be null (single camera)
   const int32_t* pixel;           // list mode
   int32_t fixed_cam;              // >= 0: every ray belongs to this camera
+  int32_t random;                 // 1: rays are random pixels of fixed_cam (see below)
+  uint64_t seed;                  // random mode: generator seed
+  const double* iter;             // random mode: device iteration counter (an integer)
 };
+
+// SplitMix64 output function (Steele, Lea and Flood, 2014) used as a
+// counter-based generator: value k of stream `seed` is
+// mix(seed + (k + 1) * 0x9E3779B97F4A7C15).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
 
 #ifndef PLX_BLK_SHIFT
 #define PLX_BLK_SHIFT 3
@@ -148,7 +161,18 @@ __device__ __forceinline__ RayId ray_of(const Common& P, int64_t tile, int lane)
     r.out = i;
     r.cam = 0;
     r.u = r.v = 0;
-    if (r.valid) {
+    if (r.valid && P.rl.random) {
+      // random mode: ray i of iteration t is pixel splitmix64(seed, t n + i) mod (W H)
+      // of the fixed camera; its targets are the full frame's row of that pixel
+      const int c = P.rl.fixed_cam;
+      const uint64_t t = (uint64_t)__ldg(P.rl.iter);
+      const uint64_t npx = (uint64_t)P.ct.cam[c].width * P.ct.cam[c].height;
+      const int pix = (int)(splitmix64(P.rl.seed, t * (uint64_t)P.ct.n_rays + (uint64_t)i) % npx);
+      r.cam = c;
+      r.u = pix % P.ct.cam[c].width;
+      r.v = pix / P.ct.cam[c].width;
+      r.out = pix;
+    } else if (r.valid) {
       const int c = P.rl.fixed_cam >= 0 ? P.rl.fixed_cam
                     : (P.rl.cam_id ? __ldg(P.rl.cam_id + i) : 0);
       const int pix = __ldg(P.rl.pixel + i);
@@ -525,5 +549,46 @@ __device__ __forceinline__ void alpha_of(float x, float& alpha, float& keep) {
 }
 
 __device__ __forceinline__ bool depth_valid(float d) { return isfinite(d) && d > 0.f; }
+
+// pose <- exp(xi^) pose for the twist xi = (rho, phi) (Sec. 5.3: the pose is
+// optimised directly): Rodrigues' rotation, translation V rho, composed on the
+// left of the row-major 3x4 camera-to-world pose. FP64.
+__device__ __forceinline__ void se3_exp_left(const double xi[6], double* pose) {
+  const double px = xi[3], py = xi[4], pz = xi[5];
+  const double th2 = px * px + py * py + pz * pz;
+  double A, B, Cc;
+  if (th2 < 1e-12) {
+    A = 1.0 - th2 / 6.0;
+    B = 0.5 - th2 / 24.0;
+    Cc = 1.0 / 6.0 - th2 / 120.0;
+  } else {
+    const double th = sqrt(th2);
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    A = sn / th;
+    B = (1.0 - cs) / th2;
+    Cc = (th - sn) / (th2 * th);
+  }
+  const double K[3][3] = {{0.0, -pz, py}, {pz, 0.0, -px}, {-py, px, 0.0}};
+  double R[3][3], t[3];
+  for (int i = 0; i < 3; ++i) {
+    t[i] = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      double k2 = 0.0;
+      for (int m = 0; m < 3; ++m) k2 += K[i][m] * K[m][j];
+      const double I = i == j ? 1.0 : 0.0;
+      R[i][j] = I + A * K[i][j] + B * k2;
+      t[i] += (I + B * K[i][j] + Cc * k2) * xi[j];
+    }
+  }
+  double out[12];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = j == 3 ? t[i] : 0.0;
+      for (int m = 0; m < 3; ++m) s += R[i][m] * pose[4 * m + j];
+      out[4 * i + j] = s;
+    }
+  for (int q = 0; q < 12; ++q) pose[q] = out[q];
+}
 
 }  // namespace plx

@@ -130,42 +130,7 @@ __global__ void k_pose_step(const double* __restrict__ H, const double* __restri
     for (int k = i + 1; k < 6; ++k) s -= L[k][i] * xi[k];
     xi[i] = s / L[i][i];
   }
-  // SE(3) exponential of (rho, phi)
-  const double px = xi[3], py = xi[4], pz = xi[5];
-  const double th2 = px * px + py * py + pz * pz;
-  double A, B, Cc;
-  if (th2 < 1e-12) {
-    A = 1.0 - th2 / 6.0;
-    B = 0.5 - th2 / 24.0;
-    Cc = 1.0 / 6.0 - th2 / 120.0;
-  } else {
-    const double th = sqrt(th2);
-    double sn, cs;
-    sincos(th, &sn, &cs);
-    A = sn / th;
-    B = (1.0 - cs) / th2;
-    Cc = (th - sn) / (th2 * th);
-  }
-  const double K[3][3] = {{0.0, -pz, py}, {pz, 0.0, -px}, {-py, px, 0.0}};
-  double R[3][3], t[3];
-  for (int i = 0; i < 3; ++i) {
-    t[i] = 0.0;
-    for (int j = 0; j < 3; ++j) {
-      double k2 = 0.0;
-      for (int m = 0; m < 3; ++m) k2 += K[i][m] * K[m][j];
-      const double I = i == j ? 1.0 : 0.0;
-      R[i][j] = I + A * K[i][j] + B * k2;
-      t[i] += (I + B * K[i][j] + Cc * k2) * xi[j];
-    }
-  }
-  double out[12];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 4; ++j) {
-      double s = j == 3 ? t[i] : 0.0;
-      for (int m = 0; m < 3; ++m) s += R[i][m] * pose[4 * m + j];
-      out[4 * i + j] = s;
-    }
-  for (int q = 0; q < 12; ++q) pose[q] = out[q];
+  se3_exp_left(xi, pose);
   if (xi_out)
     for (int q = 0; q < 6; ++q) xi_out[q] = xi[q];
   if (status) *status = 0;

@@ -71,7 +71,8 @@ class RenderOpts(C.Structure):
 SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload",
            "plx_grid_download", "plx_grid_info", "plx_grid_destroy", "plx_render_forward",
            "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
-           "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch"]
+           "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch",
+           "plx_grid_rmsprop", "plx_track_adam_step"]
 
 
 def _load():
@@ -96,6 +97,9 @@ def _load():
         "plx_render_backward_pose": [P, C.POINTER(Cameras), I32, C.POINTER(Rays),
                                      C.POINTER(RenderOpts), P, P, P, P, P, P],
         "plx_pose_step": [P, P, D, P, P, P, P],
+        "plx_grid_rmsprop": [P, P, P, C.c_float, C.c_float, C.c_float, I32, P],
+        "plx_track_adam_step": [P, C.POINTER(Cameras), I32, C.POINTER(RenderOpts), I32, C.c_uint64,
+                                P, P, P, D, D, D, D, P, P, P, P],
         "plx_render_batch": [P, C.POINTER(Cameras), C.POINTER(Work), I32, C.POINTER(RenderOpts),
                              P, P, P, P, P, P, P, P],
         "plx_render_backward_pose_noalloc": [C.POINTER(GridDesc), P, P, C.POINTER(Cameras), I32,
@@ -350,3 +354,31 @@ def render_batch(grid: Grid, cams: CameraSet, work, opts, rgb_target, depth_targ
                                  _ptr(map_loss), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
                                  _stream(stream)))
     return grad, map_loss, out[0][:n_track], out[1][:n_track], out[2][:n_track]
+
+
+def grid_rmsprop(grid: Grid, grad, state, lr, alpha=0.99, eps=1e-8, zero_grad=True, stream=None):
+    """plx_grid_rmsprop: one RMSProp step on every stored grid value, in place."""
+    _check(_lib.plx_grid_rmsprop(grid.handle, _ptr(grad), _ptr(state), float(lr), float(alpha),
+                                 float(eps), int(bool(zero_grad)), _stream(stream)))
+
+
+def adam_state():
+    """Zeroed Adam tracking state (m, v, t, last xi) for plx_track_adam_step."""
+    return torch.zeros(20, device="cuda", dtype=torch.float64)
+
+
+def track_adam_step(grid: Grid, cams: CameraSet, cam: int, opts, n_rays, seed, rgb_target,
+                    depth_target, state, lr, beta1=0.9, beta2=0.999, eps=1e-8, out=None,
+                    stream=None):
+    """plx_track_adam_step: one Adam iteration on random rays of camera ``cam``."""
+    if out is None:
+        out = (torch.empty(6, 6, device="cuda", dtype=torch.float64),
+               torch.empty(6, device="cuda", dtype=torch.float64),
+               torch.empty(2, device="cuda", dtype=torch.float64))
+    cs = cams.struct()
+    _check(_lib.plx_track_adam_step(grid.handle, C.byref(cs), int(cam), C.byref(opts),
+                                    int(n_rays), C.c_uint64(seed), _ptr(rgb_target),
+                                    _ptr(depth_target), _ptr(state), float(lr), float(beta1),
+                                    float(beta2), float(eps), _ptr(out[0]), _ptr(out[1]),
+                                    _ptr(out[2]), _stream(stream)))
+    return out
