@@ -418,6 +418,55 @@ def run_tracking(args, world, rank, barrier):
                         "start_pose_err": float(np.abs(T0 - cam.T_wc).max()),
                         "final_pose_err": err, "final_loss": float(loss[0].item())}
         grid.close()
+    # the paper's tracker (Sec. 5.4): Adam on random rays of the frame
+    n_rays, lr, aiters = args.adam_rays, args.adam_lr, args.adam_iters
+    for storage in ("f32", "bf16"):
+        grid = plx.Grid.from_scene(sc.grid, storage)
+        cams = plx.CameraSet([cam])
+        tg = plx.render_forward(grid, cams, o)
+        rgb_t, depth_t = tg["rgb"].clone(), tg["depth"].clone()
+        start = torch.tensor(T0.reshape(1, 12), device="cuda")
+        cams.poses.copy_(start)
+        state = plx.adam_state()
+        buf = (torch.empty(6, 6, device="cuda", dtype=torch.float64),
+               torch.empty(6, device="cuda", dtype=torch.float64),
+               torch.empty(2, device="cuda", dtype=torch.float64))
+        plx.track_adam_step(grid, cams, 0, o, n_rays, 3, rgb_t, depth_t, state, lr, out=buf)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(aiters):
+                plx.track_adam_step(grid, cams, 0, o, n_rays, 3, rgb_t, depth_t, state, lr, out=buf)
+        for _ in range(args.warmup):
+            cams.poses.copy_(start)
+            state.zero_()
+            g.replay()
+        barrier()
+        evs = []
+        for _ in range(max(1, args.steps // 2)):
+            cams.poses.copy_(start)
+            state.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            evs.append((e0, e1))
+        barrier()
+        ms = [a.elapsed_time(b_) for a, b_ in evs]
+        T = cams.poses[0].cpu().numpy().reshape(3, 4)
+        out.setdefault("adam", {"rays_per_iter": n_rays, "lr": lr, "iters_per_frame": aiters,
+                                "sampler": "SplitMix64 over the frame's pixels"})
+        out["adam"][storage] = {
+            "value": aiters * len(ms) / (sum(ms) / 1e3), "unit": "iters/s",
+            "ms_per_frame": sum(ms) / len(ms),
+            "start_err_cm_deg": [float(100 * np.abs(T0[:, 3] - cam.T_wc[:, 3]).max()),
+                                 float(np.degrees(np.abs(T0[:, :3] - cam.T_wc[:, :3]).max()))],
+            "final_err_cm_deg": [float(100 * np.abs(T[:, 3] - cam.T_wc[:, 3]).max()),
+                                 float(np.degrees(np.abs(T[:, :3] - cam.T_wc[:, :3]).max()))],
+            "final_loss": float(buf[2][0].item())}
+        grid.close()
     out["value"] = out["f32"]["value"]
     return out
 
@@ -583,6 +632,9 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16", "f32_bf16"])
     ap.add_argument("--tracking-workload", default="room512")
     ap.add_argument("--tracking-iters", type=int, default=100)
+    ap.add_argument("--adam-rays", type=int, default=1024)
+    ap.add_argument("--adam-lr", type=float, default=1e-3)
+    ap.add_argument("--adam-iters", type=int, default=200)
     ap.add_argument("--no-tracking", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
