@@ -201,8 +201,16 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    tune_cache = os.path.join("/tmp", f"plx_tuning_{os.getpid()}.json")
+
     def measure(storage, K, W, with_e2e):
         grid = plx.Grid.from_scene(sc.grid, storage)
+        tuned = None
+        if not args.no_tune:
+            from paper_2307_03404_b300 import autotune
+
+            tuned = autotune.tune_mapping(grid, cams, o, rgb_t, depth_t, reps=3, cache=tune_cache)
+            log(f"[bench] {storage} mapping launch config {tuned['config']} ({tuned['ms']:.2f} ms)")
         fw = {"rgb": torch.empty(n_rays, 3, device="cuda"),
               "depth": torch.empty(n_rays, device="cuda"),
               "state": torch.empty(n_rays, device="cuda"), "counts": None}
@@ -235,7 +243,8 @@ def run_ours(args):
         fwd_ms = [e[0].elapsed_time(e[1]) for e in E]
         bwd_ms = [e[1].elapsed_time(e[2]) for e in E]
         res = {"step_ms": step_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
-               "loss": loss.cpu().tolist()}
+               "loss": loss.cpu().tolist(), "launch_config": grid.get_config(),
+               "tuning_trials": tuned["trials"] if tuned else None}
         if with_e2e:
             rgb_h = torch.from_numpy(rgb_np).pin_memory()
             depth_h = torch.from_numpy(depth_np).pin_memory()
@@ -344,6 +353,8 @@ def run_ours(args):
                         "step_frac": (fo_b + bo_b) / (hbm * 1e9) * 1e3 / (t_other / K)},
         "loss": main["loss"],
         "kernels_ms": {"forward": fwd_ms, "backward_grid": bwd_ms},
+        "launch_config": {"autotuned": not args.no_tune, args.storage: main["launch_config"],
+                          other_storage: other["launch_config"]},
         "kernel_source_sha": kernel_source_sha(),
     }
     if not args.no_tracking:
@@ -382,6 +393,12 @@ def run_tracking(args, world, rank, barrier):
         cams = plx.CameraSet([cam])
         tg = plx.render_forward(grid, cams, o)       # targets at the true pose
         rgb_t, depth_t = tg["rgb"].clone(), tg["depth"].clone()
+        if not args.no_tune:
+            from paper_2307_03404_b300 import autotune
+
+            cams.poses.copy_(torch.tensor(T0.reshape(1, 12), device="cuda"))
+            autotune.tune_tracking(grid, cams, 0, o, rgb_t, depth_t, reps=3,
+                                   cache=os.path.join("/tmp", f"plx_tuning_{os.getpid()}.json"))
         cams.poses.copy_(torch.tensor(T0.reshape(1, 12), device="cuda"))
         start = cams.poses.clone()
         H = torch.empty(6, 6, device="cuda", dtype=torch.float64)
@@ -415,6 +432,7 @@ def run_tracking(args, world, rank, barrier):
         err = float(np.abs(pose.cpu().numpy().reshape(3, 4) - cam.T_wc).max())
         out[storage] = {"value": iters * len(ms) / (sum(ms) / 1e3),
                         "ms_per_iter": sum(ms) / len(ms) / iters,
+                        "launch_config": grid.get_config(),
                         "start_pose_err": float(np.abs(T0 - cam.T_wc).max()),
                         "final_pose_err": err, "final_loss": float(loss[0].item())}
         grid.close()
@@ -522,6 +540,11 @@ def run_batch_bench(args, barrier):
 
     for storage in ("bf16", "f32"):
         grid = plx.Grid.from_scene(sc.grid, storage)
+        if not args.no_tune:
+            from paper_2307_03404_b300 import autotune
+
+            autotune.tune_batch(grid, cams, work, o, rgb_t, depth_t, reps=2,
+                                cache=os.path.join("/tmp", f"plx_tuning_{os.getpid()}.json"))
         grad = torch.zeros(grid.n_alloc, plx.GRAD_STRIDE, device="cuda")
         mloss = torch.empty(2, device="cuda", dtype=torch.float64)
         bo = (torch.empty(32, 6, 6, device="cuda", dtype=torch.float64),
@@ -548,6 +571,7 @@ def run_batch_bench(args, barrier):
         ms_b = timed(batch, max(2, args.steps // 2), args.warmup)
         ms_s = timed(separate, max(2, args.steps // 2), args.warmup)
         out[storage] = {"value": rows / (ms_b / 1e3), "ms_per_batch": ms_b,
+                        "launch_config": grid.get_config(),
                         "separate_calls": {"value": rows / (ms_s / 1e3), "ms": ms_s,
                                            "launches": 3 + 32}}
         grid.close()
@@ -638,6 +662,7 @@ def main():
     ap.add_argument("--no-tracking", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-rays-per-step", type=int, default=512)
     args = ap.parse_args()

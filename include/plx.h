@@ -302,6 +302,31 @@ plx_status plx_track_adam_step(const plx_grid *grid, const plx_cameras *cams,
                                double eps, double *JtWJ, double *JtWr,
                                double *loss, void *stream);
 
+/* Launch choices of a grid's kernels (the paper has none; they do not change
+ * any result). block_shift: the empty-space map marks blocks of
+ * 2^block_shift cells per axis (1..6); rays jump over blocks without an
+ * allocated vertex. *_blocks: each ray kernel is compiled for 1 or 2
+ * resident blocks of 256 threads per SM (a register budget of 255 or 128 per
+ * thread): forward, grid adjoint, pose Jacobian, batched launch. Defaults are
+ * the best measured on B300 for room-scale grids; the Python autotuner times
+ * the alternatives on a caller's workload. */
+typedef struct {
+  int32_t block_shift;
+  int32_t forward_blocks;
+  int32_t adjoint_blocks;
+  int32_t pose_blocks;
+  int32_t batch_blocks;
+} plx_launch_config;
+
+/* Current launch choices of a grid (HOST out). */
+plx_status plx_grid_get_config(const plx_grid *grid, plx_launch_config *out);
+
+/* Sets the launch choices. A new block_shift rebuilds the empty-space map
+ * (allocates, synchronises `stream`); otherwise nothing runs on the device.
+ * Errors: PLX_EINVAL (out of range), PLX_ENOMEM, PLX_ECUDA. */
+plx_status plx_grid_set_config(plx_grid *grid, const plx_launch_config *config,
+                               void *stream);
+
 /* Kinds of work in a batch. */
 typedef enum { PLX_WORK_MAP = 0, PLX_WORK_TRACK = 1 } plx_work_mode;
 

@@ -12,23 +12,23 @@
 #include "plx_internal.cuh"
 
 namespace plx {
-void launch_forward(int store, const Common& P, float* rgb, float* depth, float* state,
+void launch_forward(int store, int minb, const Common& P, float* rgb, float* depth, float* state,
                     int32_t* counts, cudaStream_t s);
-void launch_backward_grid(int store, const Common& P, const float* rgb_t, const float* depth_t,
-                          const float* rgb, const float* depth, float* grad, double* loss_out,
-                          unsigned long long* M, int num_sms, cudaStream_t s);
-void launch_backward_pose(int store, const Common& P, const float* rgb_t, const float* depth_t,
-                          double* partials, unsigned* retire, double* JtWJ, double* JtWr,
-                          double* loss, int max_blocks, cudaStream_t s);
+void launch_backward_grid(int store, int minb, const Common& P, const float* rgb_t,
+                          const float* depth_t, const float* rgb, const float* depth, float* grad,
+                          double* loss_out, unsigned long long* M, int num_sms, cudaStream_t s);
+void launch_backward_pose(int store, int minb, const Common& P, const float* rgb_t,
+                          const float* depth_t, double* partials, unsigned* retire, double* JtWJ,
+                          double* JtWr, double* loss, int max_blocks, cudaStream_t s);
 void launch_pose_step(const double* H, const double* b, double damping, double* pose,
                       double* xi_out, int32_t* status, cudaStream_t s);
-int pose_kernel_blocks_per_sm(int store);
-int batch_kernel_blocks_per_sm(int store);
+int pose_kernel_blocks_per_sm(int store, int minb);
+int batch_kernel_blocks_per_sm(int store, int minb);
 void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, float lr,
                     float alpha, float eps, int zero_grad, int num_sms, cudaStream_t s);
 void launch_adam_pose(const double* JtWr, double* state, double* pose, double lr, double b1,
                       double b2, double eps, cudaStream_t s);
-void launch_batch(int store, const Common& P, int n_track, const float* rgb_t,
+void launch_batch(int store, int minb, const Common& P, int n_track, const float* rgb_t,
                   const float* depth_t, float* grad, double* map_loss, double* JtWJ, double* JtWr,
                   double* track_loss, unsigned long long* Mmap, double* track_acc,
                   unsigned long long* counter, int blocks, int num_sms, cudaStream_t s);
@@ -56,8 +56,10 @@ struct plx_grid {
   int nb[3] = {0, 0, 0};
   int rec_bytes = 0;
   char* ws = nullptr;
-  int max_pose_blocks = 0;
-  int batch_blocks[4] = {0, 0, 0, 0};
+  int max_pose_blocks = 0;        // partials the workspace holds (max over variants)
+  plx_launch_config cfg;          // launch choices (autotuner)
+  int pose_blocks = 0;            // resident blocks of the chosen pose variant
+  int batch_blocks = 0;           // resident blocks of the chosen batch variant
   int num_sms = 0;
   int device = 0;
   double inv_h[3];
@@ -169,7 +171,7 @@ __global__ void k_check_links(const int32_t* __restrict__ links, int64_t n, int6
 // Marks every 8^3-cell block that has a cell with an allocated corner: vertex
 // x is a corner of cells x-1 and x (those that exist), on each axis.
 __global__ void k_build_blocks(const int32_t* __restrict__ links, int rx, int ry, int rz,
-                               uint8_t* __restrict__ blk, int nbx, int nby) {
+                               uint8_t* __restrict__ blk, int nbx, int nby, int sh) {
   const int64_t n = (int64_t)rx * ry * rz;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -181,7 +183,7 @@ __global__ void k_build_blocks(const int32_t* __restrict__ links, int rx, int ry
     for (int cz = z0; cz <= z1; ++cz)
       for (int cy = y0; cy <= y1; ++cy)
         for (int cx = x0; cx <= x1; ++cx)
-          blk[((int64_t)(cz >> kBlkShift) * nby + (cy >> kBlkShift)) * nbx + (cx >> kBlkShift)] = 1;
+          blk[((int64_t)(cz >> sh) * nby + (cy >> sh)) * nbx + (cx >> sh)] = 1;
   }
 }
 
@@ -189,6 +191,41 @@ static unsigned grid_stride_blocks(int64_t n, int num_sms) {
   const int64_t want = (n + 255) / 256;
   const int64_t cap = (int64_t)num_sms * 8;
   return (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+// (Re)builds the empty-space map of `g` for blocks of 2^shift cells.
+static cudaError_t build_block_map(plx_grid* g, int shift, cudaStream_t s) {
+  int nb[3];
+  for (int a = 0; a < 3; ++a) nb[a] = ((g->desc.res[a] - 1) + (1 << shift) - 1) >> shift;
+  const size_t bytes = (size_t)nb[0] * nb[1] * nb[2];
+  uint8_t* blk = nullptr;
+  cudaError_t e = cudaMalloc(&blk, bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(blk, 0, bytes, s);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    return e;
+  }
+  const int64_t n_links = (int64_t)g->desc.res[0] * g->desc.res[1] * g->desc.res[2];
+  k_build_blocks<<<grid_stride_blocks(n_links, g->num_sms), 256, 0, s>>>(
+      g->links, g->desc.res[0], g->desc.res[1], g->desc.res[2], blk, nb[0], nb[1], shift);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    return e;
+  }
+  cudaFree(g->blk);
+  g->blk = blk;
+  for (int a = 0; a < 3; ++a) g->nb[a] = nb[a];
+  g->cfg.block_shift = shift;
+  return cudaSuccess;
+}
+
+// Resident blocks of the chosen pose and batch variants.
+static void apply_config(plx_grid* g) {
+  g->pose_blocks = g->num_sms * pose_kernel_blocks_per_sm(g->desc.storage, g->cfg.pose_blocks);
+  g->batch_blocks = g->num_sms * batch_kernel_blocks_per_sm(g->desc.storage, g->cfg.batch_blocks);
+  if (g->pose_blocks > g->max_pose_blocks) g->pose_blocks = g->max_pose_blocks;
 }
 
 // ------------------------------------------------------------------- ABI
@@ -234,33 +271,33 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
   if (e != cudaSuccess) return cleanup(fail(PLX_ECUDA, "grid_create: %s", cudaGetErrorString(e)));
   int bps = 1;
-  for (int st = 0; st < 4; ++st) {
-    const int b = pose_kernel_blocks_per_sm(st);
+  for (int m = 1; m <= 2; ++m) {
+    const int b = pose_kernel_blocks_per_sm(desc->storage, m);
     bps = b > bps ? b : bps;
   }
   g->max_pose_blocks = g->num_sms * bps;
-  for (int st = 0; st < 4; ++st) g->batch_blocks[st] = g->num_sms * batch_kernel_blocks_per_sm(st);
+  g->cfg.block_shift = kDefaultBlkShift;
+  g->cfg.forward_blocks = kDefaultFwdBlocks;
+  g->cfg.adjoint_blocks = kDefaultBwdBlocks;
+  g->cfg.pose_blocks = kDefaultPoseBlocks;
+  g->cfg.batch_blocks = kDefaultBatchBlocks;
+  apply_config(g);
   const size_t ws_bytes = sizeof(Workspace) +
                           ((size_t)g->max_pose_blocks + PLX_MAX_CAMERAS) * 32 * sizeof(double);
   e = cudaMalloc(&g->links, (size_t)n_links * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&g->rec, (size_t)(desc->n_alloc > 0 ? desc->n_alloc : 1) * g->rec_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&g->ws, ws_bytes);
-  for (int a = 0; a < 3; ++a) g->nb[a] = ((desc->res[a] - 1) + (1 << kBlkShift) - 1) >> kBlkShift;
-  const size_t blk_bytes = (size_t)g->nb[0] * g->nb[1] * g->nb[2];
-  if (e == cudaSuccess) e = cudaMalloc(&g->blk, blk_bytes);
   if (e != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA,
                         "grid_create: allocation failed: %s", cudaGetErrorString(e)));
   e = cudaMemsetAsync(g->ws, 0, ws_bytes, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g->blk, 0, blk_bytes, s);
+
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->links, links, (size_t)n_links * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cleanup(fail(PLX_ECUDA, "grid_create: %s", cudaGetErrorString(e)));
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
   k_check_links<<<grid_stride_blocks(n_links, g->num_sms), 256, 0, s>>>(g->links, n_links,
                                                                       desc->n_alloc, &ws->err);
-  k_build_blocks<<<grid_stride_blocks(n_links, g->num_sms), 256, 0, s>>>(
-      links, desc->res[0], desc->res[1], desc->res[2], g->blk, g->nb[0], g->nb[1]);
   if (desc->n_alloc > 0)
     k_repack<<<grid_stride_blocks(desc->n_alloc, g->num_sms), 256, 0, s>>>(
         density, sh, desc->n_alloc, desc->storage, g->rec);
@@ -270,6 +307,10 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cleanup(fail(PLX_ECUDA, "grid_create: %s", cudaGetErrorString(e)));
   if (err) return cleanup(fail(PLX_EINVAL, "grid_create: a link is outside [-1, n_alloc)"));
+  e = build_block_map(g, kDefaultBlkShift, s);
+  if (e != cudaSuccess)
+    return cleanup(fail(e == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA,
+                        "grid_create: empty-space map: %s", cudaGetErrorString(e)));
   *out = g;
   return PLX_OK;
 }
@@ -346,6 +387,7 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
   P.g.blk = g->blk;
   P.g.nbx = g->nb[0];
   P.g.nby = g->nb[1];
+  P.g.blk_shift = g->cfg.block_shift;
   P.g.rx = g->desc.res[0];
   P.g.ry = g->desc.res[1];
   P.g.rz = g->desc.res[2];
@@ -436,7 +478,7 @@ plx_status plx_render_forward(const plx_grid* g, const plx_cameras* cams, const 
   if (st != PLX_OK) return st;
   if (P.ct.n_rays > 0 && (!rgb_out || !depth_out))
     return fail(PLX_EINVAL, "render_forward: null rgb_out or depth_out");
-  launch_forward(g->desc.storage, P, rgb_out, depth_out, state_out, counts_out,
+  launch_forward(g->desc.storage, g->cfg.forward_blocks, P, rgb_out, depth_out, state_out, counts_out,
                  (cudaStream_t)stream);
   return launch_check("render_forward");
 }
@@ -454,7 +496,7 @@ plx_status plx_render_backward_grid(const plx_grid* g, const plx_cameras* cams,
   if (reinterpret_cast<uintptr_t>(grad) % 16 != 0)
     return fail(PLX_EINVAL, "render_backward_grid: grad must be 16-byte aligned");
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
-  launch_backward_grid(g->desc.storage, P, rgb_target, depth_target, rgb, depth, grad, loss_out,
+  launch_backward_grid(g->desc.storage, g->cfg.adjoint_blocks, P, rgb_target, depth_target, rgb, depth, grad, loss_out,
                        &ws->M, g->num_sms, (cudaStream_t)stream);
   return launch_check("render_backward_grid");
 }
@@ -472,8 +514,8 @@ plx_status plx_render_backward_pose(const plx_grid* g, const plx_cameras* cams, 
     return fail(PLX_EINVAL, "render_backward_pose: null target");
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
   double* partials = reinterpret_cast<double*>(g->ws + sizeof(Workspace));
-  launch_backward_pose(g->desc.storage, P, rgb_target, depth_target, partials, &ws->retire, JtWJ,
-                       JtWr, loss, g->max_pose_blocks, (cudaStream_t)stream);
+  launch_backward_pose(g->desc.storage, g->cfg.pose_blocks, P, rgb_target, depth_target, partials,
+                       &ws->retire, JtWJ, JtWr, loss, g->pose_blocks, (cudaStream_t)stream);
   return launch_check("render_backward_pose");
 }
 
@@ -487,6 +529,33 @@ plx_status plx_pose_step(const double* JtWJ, const double* JtWr, double damping,
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ launch config
+extern "C" plx_status plx_grid_get_config(const plx_grid* g, plx_launch_config* out) {
+  if (!g || !out) return fail(PLX_EINVAL, "grid_get_config: null argument");
+  *out = g->cfg;
+  return PLX_OK;
+}
+
+extern "C" plx_status plx_grid_set_config(plx_grid* g, const plx_launch_config* c, void* stream) {
+  const char* what = "grid_set_config";
+  if (!g || !c) return fail(PLX_EINVAL, "%s: null argument", what);
+  if (c->block_shift < 1 || c->block_shift > 6)
+    return fail(PLX_EINVAL, "%s: block_shift %d out of [1, 6]", what, c->block_shift);
+  const int v[4] = {c->forward_blocks, c->adjoint_blocks, c->pose_blocks, c->batch_blocks};
+  for (int i = 0; i < 4; ++i)
+    if (v[i] != 1 && v[i] != 2)
+      return fail(PLX_EINVAL, "%s: blocks per SM must be 1 or 2", what);
+  if (c->block_shift != g->cfg.block_shift) {
+    const cudaError_t e = build_block_map(g, c->block_shift, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+      return fail(e == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA, "%s: %s", what,
+                  cudaGetErrorString(e));
+  }
+  g->cfg = *c;
+  apply_config(g);
+  return PLX_OK;
+}
 
 // ------------------------------------------------------------ batched work
 extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cams,
@@ -548,8 +617,8 @@ extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cam
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
   double* track_acc =
       reinterpret_cast<double*>(g->ws + sizeof(Workspace)) + (size_t)g->max_pose_blocks * 32;
-  launch_batch(g->desc.storage, P, n_track, rgb_target, depth_target, grad, map_loss, JtWJ, JtWr,
-               track_loss, &ws->M_map, track_acc, &ws->tile_counter, g->batch_blocks[g->desc.storage],
+  launch_batch(g->desc.storage, g->cfg.batch_blocks, P, n_track, rgb_target, depth_target, grad, map_loss, JtWJ, JtWr,
+               track_loss, &ws->M_map, track_acc, &ws->tile_counter, g->batch_blocks,
                g->num_sms, (cudaStream_t)stream);
   return launch_check(what);
 }
@@ -600,8 +669,8 @@ extern "C" plx_status plx_track_adam_step(const plx_grid* g, const plx_cameras* 
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
   double* partials = reinterpret_cast<double*>(g->ws + sizeof(Workspace));
   cudaStream_t s = (cudaStream_t)stream;
-  launch_backward_pose(g->desc.storage, P, rgb_target, depth_target, partials, &ws->retire, JtWJ,
-                       JtWr, loss, g->max_pose_blocks, s);
+  launch_backward_pose(g->desc.storage, g->cfg.pose_blocks, P, rgb_target, depth_target, partials,
+                       &ws->retire, JtWJ, JtWr, loss, g->pose_blocks, s);
   launch_adam_pose(JtWr, state, const_cast<double*>(cams->poses) + 12 * cam, lr, beta1, beta2, eps,
                    s);
   return launch_check(what);
@@ -638,7 +707,7 @@ static plx_status noalloc_setup(int dev, int storage, char** ptr, int* max_block
     if (e != cudaSuccess)
       return fail(PLX_ECUDA, "render_backward_pose_noalloc: %s", cudaGetErrorString(e));
     for (int st = 0; st < 4; ++st) {
-      const int b = sms * pose_kernel_blocks_per_sm(st);
+      const int b = sms * pose_kernel_blocks_per_sm(st, kDefaultPoseBlocks);
       g_noalloc_blocks[dev][st] = b < PLX_NOALLOC_MAX_BLOCKS ? b : PLX_NOALLOC_MAX_BLOCKS;
     }
     g_noalloc_ptr[dev] = static_cast<char*>(p);
@@ -686,6 +755,7 @@ extern "C" plx_status plx_render_backward_pose_noalloc(
   view.rec = const_cast<void*>(records);
   view.rec_bytes = record_bytes(desc->storage);
   view.ws = scratch;
+  view.cfg.block_shift = kDefaultBlkShift;  // unused: the view has no empty-space map
   for (int a = 0; a < 3; ++a) view.inv_h[a] = (double)(desc->res[a] - 1) / (desc->hi[a] - desc->lo[a]);
   Common P;
   st = build_common(what, &view, cams, rays, opts, cam, P);
@@ -697,7 +767,7 @@ extern "C" plx_status plx_render_backward_pose_noalloc(
   Workspace* ws = reinterpret_cast<Workspace*>(scratch);
   e = cudaMemsetAsync(ws, 0, sizeof(Workspace), s);  // error word and retirement counter
   if (e != cudaSuccess) return fail(PLX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-  launch_backward_pose(desc->storage, P, rgb_target, depth_target,
+  launch_backward_pose(desc->storage, kDefaultPoseBlocks, P, rgb_target, depth_target,
                        reinterpret_cast<double*>(scratch + sizeof(Workspace)), &ws->retire, JtWJ,
                        JtWr, loss, max_blocks, s);
   return launch_check(what);

@@ -19,10 +19,6 @@
 #include "plx_march.cuh"
 #include "plx_pose_march.cuh"
 
-#ifndef PLX_BATCH_MIN_BLOCKS
-#define PLX_BATCH_MIN_BLOCKS 1
-#endif
-
 namespace plx {
 
 // Valid rays of the mapping items (their loss normaliser M), walking the same
@@ -43,8 +39,8 @@ __global__ void k_count_batch(const __grid_constant__ Common P, const float* __r
   if (lane == 0 && local) atomicAdd(M, local);
 }
 
-template <int STORE>
-__global__ void __launch_bounds__(kBlock, PLX_BATCH_MIN_BLOCKS)
+template <int STORE, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
 k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
         const float* __restrict__ depth_t, float* __restrict__ grad, double* __restrict__ map_loss,
         const unsigned long long* __restrict__ Mmap, double* __restrict__ track_acc,
@@ -130,15 +126,7 @@ __global__ void k_batch_finalize(const double* __restrict__ track_acc, int n_tra
   track_loss[2 * f + 1] = M;
 }
 
-template <int STORE>
-static void launch_batch_t(const Common& P, const float* rgb_t, const float* depth_t, float* grad,
-                           double* map_loss, unsigned long long* Mmap, double* track_acc,
-                           unsigned long long* counter, int blocks, cudaStream_t s) {
-  k_batch<STORE><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, grad, map_loss, Mmap, track_acc,
-                                           counter);
-}
-
-void launch_batch(int store, const Common& P, int n_track, const float* rgb_t,
+void launch_batch(int store, int minb, const Common& P, int n_track, const float* rgb_t,
                   const float* depth_t, float* grad, double* map_loss, double* JtWJ, double* JtWr,
                   double* track_loss, unsigned long long* Mmap, double* track_acc,
                   unsigned long long* counter, int blocks, int num_sms, cudaStream_t s) {
@@ -152,45 +140,22 @@ void launch_batch(int store, const Common& P, int n_track, const float* rgb_t,
     k_count_batch<<<cb, kBlock, 0, s>>>(P, depth_t, Mmap);
   }
   if (P.ct.n_tiles > 0) {
-    switch (store) {
-      case PLX_STORE_F32:
-        launch_batch_t<PLX_STORE_F32>(P, rgb_t, depth_t, grad, map_loss, Mmap, track_acc, counter,
-                                      blocks, s);
-        break;
-      case PLX_STORE_BF16:
-        launch_batch_t<PLX_STORE_BF16>(P, rgb_t, depth_t, grad, map_loss, Mmap, track_acc, counter,
-                                       blocks, s);
-        break;
-      case PLX_STORE_F16:
-        launch_batch_t<PLX_STORE_F16>(P, rgb_t, depth_t, grad, map_loss, Mmap, track_acc, counter,
-                                      blocks, s);
-        break;
-      default:
-        launch_batch_t<PLX_STORE_F32_BF16>(P, rgb_t, depth_t, grad, map_loss, Mmap, track_acc,
-                                           counter, blocks, s);
-        break;
-    }
+#define PLX_BATCH(S, M_)                                                                      \
+  k_batch<S, M_><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, grad, map_loss, Mmap, track_acc, \
+                                           counter)
+    PLX_DISPATCH_SM(store, minb, PLX_BATCH);
+#undef PLX_BATCH
   }
   const int fb = n_track > 0 ? (n_track + 127) / 128 : 1;
   k_batch_finalize<<<fb, 128, 0, s>>>(track_acc, n_track, JtWJ, JtWr, track_loss, map_loss, Mmap);
 }
 
-int batch_kernel_blocks_per_sm(int store) {
+int batch_kernel_blocks_per_sm(int store, int minb) {
   int n = 0;
-  switch (store) {
-    case PLX_STORE_F32:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<PLX_STORE_F32>, kBlock, 0);
-      break;
-    case PLX_STORE_BF16:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<PLX_STORE_BF16>, kBlock, 0);
-      break;
-    case PLX_STORE_F16:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<PLX_STORE_F16>, kBlock, 0);
-      break;
-    default:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<PLX_STORE_F32_BF16>, kBlock, 0);
-      break;
-  }
+#define PLX_OCC(S, M) \
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<S, M>, kBlock, 0)
+  PLX_DISPATCH_SM(store, minb, PLX_OCC);
+#undef PLX_OCC
   return n > 0 ? n : 1;
 }
 

@@ -29,6 +29,22 @@ constexpr int kBlock = 256;           // threads per block of the ray kernels
 constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kRecordSlots = 32;      // record = 32 slots (28 used)
 
+// Calls CALL(S, M) with S the storage mode and M (1 or 2) the blocks per SM.
+#define PLX_DISPATCH_SM(store, minb, CALL)                         \
+  do {                                                            \
+    const int key_ = (store) * 2 + ((minb) >= 2 ? 1 : 0);         \
+    switch (key_) {                                               \
+      case 0: CALL(PLX_STORE_F32, 1); break;                      \
+      case 1: CALL(PLX_STORE_F32, 2); break;                      \
+      case 2: CALL(PLX_STORE_BF16, 1); break;                     \
+      case 3: CALL(PLX_STORE_BF16, 2); break;                     \
+      case 4: CALL(PLX_STORE_F16, 1); break;                      \
+      case 5: CALL(PLX_STORE_F16, 2); break;                      \
+      case 6: CALL(PLX_STORE_F32_BF16, 1); break;                 \
+      default: CALL(PLX_STORE_F32_BF16, 2); break;                \
+    }                                                             \
+  } while (0)
+
 // ---------------------------------------------------------------- params
 struct CamParam {
   float2 inv_fx, inv_fy, cx, cy;  // 1/fx, 1/fy, principal point as (hi, lo) float pairs
@@ -68,19 +84,15 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-#ifndef PLX_BLK_SHIFT
-#define PLX_BLK_SHIFT 3
-#endif
-#ifndef PLX_FWD_MIN_BLOCKS
-#define PLX_FWD_MIN_BLOCKS 1
-#endif
-#ifndef PLX_BWD_MIN_BLOCKS
-#define PLX_BWD_MIN_BLOCKS 2
-#endif
-#ifndef PLX_POSE_MIN_BLOCKS
-#define PLX_POSE_MIN_BLOCKS 2
-#endif
-constexpr int kBlkShift = PLX_BLK_SHIFT;  // empty-space blocks of 2^shift cells per axis
+// Launch choices the autotuner can change (plx_grid_set_config). Each ray
+// kernel is compiled for 1 and 2 resident blocks per SM (register budget 255 or
+// 128 per thread); the empty-space map uses blocks of 2^shift cells per axis.
+// Defaults: the best measured on B300 for the room workloads.
+constexpr int kDefaultBlkShift = 3;
+constexpr int kDefaultFwdBlocks = 1;
+constexpr int kDefaultBwdBlocks = 2;
+constexpr int kDefaultPoseBlocks = 2;
+constexpr int kDefaultBatchBlocks = 1;
 
 struct GridView {
   const int32_t* links;           // [rz][ry][rx]
@@ -90,6 +102,7 @@ struct GridView {
   int32_t rx, ry, rz;
   int32_t n_alloc;
   int32_t nbx, nby;
+  int32_t blk_shift;              // blocks of 2^blk_shift cells per axis
   double lo[3];                   // box of the vertices
   double hi[3];
   double inv_h[3];                // 1 / spacing
@@ -479,7 +492,8 @@ __device__ __forceinline__ bool load_cell(const GridView& g, int ix, int iy, int
 // changes. Returns true if cell (ix, iy, iz) lies in such a block.
 __device__ __forceinline__ bool block_empty(const GridView& g, int ix, int iy, int iz) {
   if (!g.blk) return false;
-  const int bx = ix >> kBlkShift, by = iy >> kBlkShift, bz = iz >> kBlkShift;
+  const int sh = g.blk_shift;
+  const int bx = ix >> sh, by = iy >> sh, bz = iz >> sh;
   return __ldg(g.blk + ((int64_t)bz * g.nby + by) * g.nbx + bx) == 0;
 }
 
@@ -488,16 +502,18 @@ __device__ __forceinline__ bool block_empty(const GridView& g, int ix, int iy, i
 // ~1e-6 samples (the distance to the block face is a Sterbenz-exact
 // difference), and 0.01 samples of margin keep the jump on the safe side.
 // Always > k.
-__device__ __forceinline__ int block_exit(const RayF& r, int ix, int iy, int iz, int k) {
+__device__ __forceinline__ int block_exit(const GridView& g, const RayF& r, int ix, int iy, int iz,
+                                          int k) {
   const int c[3] = {ix, iy, iz};
+  const int sh = g.blk_shift;
   float kmin = 3.0e38f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int b = c[a] >> kBlkShift;
+    const int b = c[a] >> sh;
     if (r.sh[a] > 0.f)
-      kmin = fminf(kmin, (((float)((b + 1) << kBlkShift) - r.bh[a]) - r.bl[a]) * r.inv_s[a]);
+      kmin = fminf(kmin, (((float)((b + 1) << sh) - r.bh[a]) - r.bl[a]) * r.inv_s[a]);
     else if (r.sh[a] < 0.f)
-      kmin = fminf(kmin, (((float)(b << kBlkShift) - r.bh[a]) - r.bl[a]) * r.inv_s[a]);
+      kmin = fminf(kmin, (((float)(b << sh) - r.bh[a]) - r.bl[a]) * r.inv_s[a]);
   }
   const float kn = ceilf(kmin - 0.01f);
   return kn > (float)k ? (kn < 2.0e9f ? (int)kn : 2000000000) : k + 1;

@@ -29,7 +29,7 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
       cx = ix; cy = iy; cz = iz;
       if (block_empty(P.g, ix, iy, iz)) {
         empty = true;
-        k = block_exit(r, ix, iy, iz, k) - 1;
+        k = block_exit(P.g, r, ix, iy, iz, k) - 1;
         continue;
       }
       empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
@@ -167,7 +167,7 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
       cx = ix; cy = iy; cz = iz;
       if (skip) {
         empty = true;
-        k = block_exit(r, ix, iy, iz, k) - 1;
+        k = block_exit(P.g, r, ix, iy, iz, k) - 1;
         continue;
       }
       empty = load_cell_smem<STORE>(P.g, ix, iy, iz, Y, l, sc);

@@ -23,8 +23,8 @@
 
 namespace plx {
 
-template <int STORE>
-__global__ void __launch_bounds__(kBlock, PLX_POSE_MIN_BLOCKS)
+template <int STORE, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
 k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
                 const float* __restrict__ depth_t, double* __restrict__ partials,
                 unsigned int* __restrict__ retire, double* __restrict__ JtWJ,
@@ -137,38 +137,17 @@ __global__ void k_pose_step(const double* __restrict__ H, const double* __restri
 }
 
 // ------------------------------------------------------------ host launch
-template <int STORE>
-static void launch_pose_t(const Common& P, const float* rgb_t, const float* depth_t,
-                          double* partials, unsigned* retire, double* JtWJ, double* JtWr,
-                          double* loss, int max_blocks, cudaStream_t s) {
+void launch_backward_pose(int store, int minb, const Common& P, const float* rgb_t,
+                          const float* depth_t, double* partials, unsigned* retire, double* JtWJ,
+                          double* JtWr, double* loss, int max_blocks, cudaStream_t s) {
   int64_t want = (P.ct.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (want < 1) want = 1;
   const unsigned blocks = (unsigned)(want < max_blocks ? want : max_blocks);
-  k_backward_pose<STORE><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, partials, retire, JtWJ,
-                                                   JtWr, loss);
-}
-
-void launch_backward_pose(int store, const Common& P, const float* rgb_t, const float* depth_t,
-                          double* partials, unsigned* retire, double* JtWJ, double* JtWr,
-                          double* loss, int max_blocks, cudaStream_t s) {
-  switch (store) {
-    case PLX_STORE_F32:
-      launch_pose_t<PLX_STORE_F32>(P, rgb_t, depth_t, partials, retire, JtWJ, JtWr, loss,
-                                   max_blocks, s);
-      break;
-    case PLX_STORE_BF16:
-      launch_pose_t<PLX_STORE_BF16>(P, rgb_t, depth_t, partials, retire, JtWJ, JtWr, loss,
-                                    max_blocks, s);
-      break;
-    case PLX_STORE_F16:
-      launch_pose_t<PLX_STORE_F16>(P, rgb_t, depth_t, partials, retire, JtWJ, JtWr, loss,
-                                   max_blocks, s);
-      break;
-    default:
-      launch_pose_t<PLX_STORE_F32_BF16>(P, rgb_t, depth_t, partials, retire, JtWJ, JtWr, loss,
-                                        max_blocks, s);
-      break;
-  }
+#define PLX_POSE(S, M)                                                                 \
+  k_backward_pose<S, M><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, partials, retire, \
+                                                  JtWJ, JtWr, loss)
+  PLX_DISPATCH_SM(store, minb, PLX_POSE);
+#undef PLX_POSE
 }
 
 void launch_pose_step(const double* H, const double* b, double damping, double* pose,
@@ -176,23 +155,12 @@ void launch_pose_step(const double* H, const double* b, double damping, double* 
   k_pose_step<<<1, 32, 0, s>>>(H, b, damping, pose, xi_out, status);
 }
 
-int pose_kernel_blocks_per_sm(int store) {
+int pose_kernel_blocks_per_sm(int store, int minb) {
   int n = 0;
-  switch (store) {
-    case PLX_STORE_F32:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_backward_pose<PLX_STORE_F32>, kBlock, 0);
-      break;
-    case PLX_STORE_BF16:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_backward_pose<PLX_STORE_BF16>, kBlock, 0);
-      break;
-    case PLX_STORE_F16:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_backward_pose<PLX_STORE_F16>, kBlock, 0);
-      break;
-    default:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_backward_pose<PLX_STORE_F32_BF16>,
-                                                    kBlock, 0);
-      break;
-  }
+#define PLX_OCC(S, M) \
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_backward_pose<S, M>, kBlock, 0)
+  PLX_DISPATCH_SM(store, minb, PLX_OCC);
+#undef PLX_OCC
   return n > 0 ? n : 1;
 }
 

@@ -46,7 +46,7 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
       cx = ix; cy = iy; cz = iz;
       if (block_empty(P.g, ix, iy, iz)) {
         empty = true;
-        k = block_exit(r, ix, iy, iz, k) - 1;
+        k = block_exit(P.g, r, ix, iy, iz, k) - 1;
         continue;
       }
       empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);

@@ -20,8 +20,8 @@
 
 namespace plx {
 
-template <int STORE, bool COUNT>
-__global__ void __launch_bounds__(kBlock, PLX_FWD_MIN_BLOCKS)
+template <int STORE, bool COUNT, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
 k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __restrict__ depth,
           float* __restrict__ state, int32_t* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
@@ -65,8 +65,8 @@ __global__ void k_count_valid(const float* __restrict__ depth_t, int64_t n,
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(M, local);
 }
 
-template <int STORE>
-__global__ void __launch_bounds__(kBlock, PLX_BWD_MIN_BLOCKS)
+template <int STORE, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
 k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
                 const float* __restrict__ depth_t, const float* __restrict__ rgb,
                 const float* __restrict__ depth, float* __restrict__ grad,
@@ -115,52 +115,36 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
 }
 
 // ------------------------------------------------------------ host launch
-#define PLX_DISPATCH_STORE(store, F, ...)                                  \
-  switch (store) {                                                        \
-    case PLX_STORE_F32: F<PLX_STORE_F32>(__VA_ARGS__); break;             \
-    case PLX_STORE_BF16: F<PLX_STORE_BF16>(__VA_ARGS__); break;           \
-    case PLX_STORE_F16: F<PLX_STORE_F16>(__VA_ARGS__); break;             \
-    default: F<PLX_STORE_F32_BF16>(__VA_ARGS__); break;                   \
-  }
-
-template <int STORE>
-static void launch_forward_t(const Common& P, float* rgb, float* depth, float* state,
-                             int32_t* counts, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((P.ct.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  if (counts)
-    k_forward<STORE, true><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts);
-  else
-    k_forward<STORE, false><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts);
-}
-
-void launch_forward(int store, const Common& P, float* rgb, float* depth, float* state,
+void launch_forward(int store, int minb, const Common& P, float* rgb, float* depth, float* state,
                     int32_t* counts, cudaStream_t s) {
   if (P.ct.n_tiles == 0) return;
-  PLX_DISPATCH_STORE(store, launch_forward_t, P, rgb, depth, state, counts, s);
-}
-
-template <int STORE>
-static void launch_backward_t(const Common& P, const float* rgb_t, const float* depth_t,
-                              const float* rgb, const float* depth, float* grad,
-                              double* loss_out, const unsigned long long* M, cudaStream_t s) {
   const unsigned blocks = (unsigned)((P.ct.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  k_backward_grid<STORE><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad,
-                                                   loss_out, M);
+#define PLX_FWD(S, M)                                                               \
+  if (counts)                                                                       \
+    k_forward<S, true, M><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts);  \
+  else                                                                              \
+    k_forward<S, false, M><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts)
+  PLX_DISPATCH_SM(store, minb, PLX_FWD);
+#undef PLX_FWD
 }
 
-void launch_backward_grid(int store, const Common& P, const float* rgb_t, const float* depth_t,
-                          const float* rgb, const float* depth, float* grad, double* loss_out,
-                          unsigned long long* M, int num_sms, cudaStream_t s) {
+void launch_backward_grid(int store, int minb, const Common& P, const float* rgb_t,
+                          const float* depth_t, const float* rgb, const float* depth, float* grad,
+                          double* loss_out, unsigned long long* M, int num_sms, cudaStream_t s) {
   cudaMemsetAsync(M, 0, sizeof(unsigned long long), s);
   if (loss_out) cudaMemsetAsync(loss_out, 0, 2 * sizeof(double), s);
   if (P.ct.n_rays > 0) {
     const int64_t want = (P.ct.n_rays + kBlock - 1) / kBlock;
-    const unsigned blocks = (unsigned)(want < 4 * num_sms ? want : 4 * num_sms);
-    k_count_valid<<<blocks, kBlock, 0, s>>>(depth_t, P.ct.n_rays, M);
+    const unsigned cb = (unsigned)(want < 4 * num_sms ? want : 4 * num_sms);
+    k_count_valid<<<cb, kBlock, 0, s>>>(depth_t, P.ct.n_rays, M);
   }
   if (P.ct.n_tiles == 0) return;
-  PLX_DISPATCH_STORE(store, launch_backward_t, P, rgb_t, depth_t, rgb, depth, grad, loss_out,
-                     M, s);
+  const unsigned blocks = (unsigned)((P.ct.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
+#define PLX_BWD(S, M_)                                                                   \
+  k_backward_grid<S, M_><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad, \
+                                                  loss_out, M)
+  PLX_DISPATCH_SM(store, minb, PLX_BWD);
+#undef PLX_BWD
 }
 
 }  // namespace plx

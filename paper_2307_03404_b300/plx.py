@@ -62,6 +62,12 @@ class Work(C.Structure):
 WORK_MAP, WORK_TRACK = 0, 1
 
 
+class LaunchConfig(C.Structure):
+    _fields_ = [("block_shift", C.c_int32), ("forward_blocks", C.c_int32),
+                ("adjoint_blocks", C.c_int32), ("pose_blocks", C.c_int32),
+                ("batch_blocks", C.c_int32)]
+
+
 class RenderOpts(C.Structure):
     _fields_ = [("step", C.c_double), ("near_t", C.c_double), ("stop_T", C.c_double),
                 ("bg", C.c_float * 3), ("lambda_d", C.c_float), ("max_samples", C.c_int32),
@@ -72,7 +78,8 @@ SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload"
            "plx_grid_download", "plx_grid_info", "plx_grid_destroy", "plx_render_forward",
            "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
            "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch",
-           "plx_grid_rmsprop", "plx_track_adam_step"]
+           "plx_grid_rmsprop", "plx_track_adam_step", "plx_grid_get_config",
+           "plx_grid_set_config"]
 
 
 def _load():
@@ -97,6 +104,8 @@ def _load():
         "plx_render_backward_pose": [P, C.POINTER(Cameras), I32, C.POINTER(Rays),
                                      C.POINTER(RenderOpts), P, P, P, P, P, P],
         "plx_pose_step": [P, P, D, P, P, P, P],
+        "plx_grid_get_config": [P, C.POINTER(LaunchConfig)],
+        "plx_grid_set_config": [P, C.POINTER(LaunchConfig), P],
         "plx_grid_rmsprop": [P, P, P, C.c_float, C.c_float, C.c_float, I32, P],
         "plx_track_adam_step": [P, C.POINTER(Cameras), I32, C.POINTER(RenderOpts), I32, C.c_uint64,
                                 P, P, P, D, D, D, D, P, P, P, P],
@@ -182,6 +191,19 @@ class Grid:
 
     def check(self, stream=None):
         _check(_lib.plx_grid_check(self._h, _stream(stream)))
+
+    def get_config(self) -> dict:
+        c = LaunchConfig()
+        _check(_lib.plx_grid_get_config(self._h, C.byref(c)))
+        return {f: int(getattr(c, f)) for f, _ in LaunchConfig._fields_}
+
+    def set_config(self, stream=None, **kw):
+        """Change launch choices (block_shift, forward_blocks, adjoint_blocks,
+        pose_blocks, batch_blocks); results do not change."""
+        cur = self.get_config()
+        cur.update({k: int(v) for k, v in kw.items()})
+        c = LaunchConfig(**cur)
+        _check(_lib.plx_grid_set_config(self._h, C.byref(c), _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None):
