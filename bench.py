@@ -174,6 +174,21 @@ def workload_config(sc, cams, storage):
 
 
 # ------------------------------------------------------------------- ours
+def bytes_model(counts, storage, valid):
+    """Algorithmic bytes of the forward and the adjoint launch over these rays
+    (no reuse: every marched sample reads its 8 links, every sample with an
+    allocated corner gathers 8 records, the adjoint adds a read-modify-write of
+    8 FP32 gradient rows per such sample; per-ray I/O on top)."""
+    n_rays = counts.shape[0]
+    rec = 896.0 if storage == "f32" else 448.0
+    s_all = counts[:, 0].astype(np.float64)
+    s_occ = counts[:, 1].astype(np.float64)
+    fwd = (s_all * 32 + s_occ * rec).sum() + 20.0 * n_rays
+    bwd = (s_all[valid] * 32 + s_occ[valid] * (rec + 1792.0)).sum() + 32.0 * valid.sum() \
+        + 4.0 * n_rays
+    return fwd, bwd, float(s_all.mean()), float(s_occ.mean())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -304,22 +319,13 @@ def run_ours(args):
     valid = np.isfinite(depth_np) & (depth_np > 0)
     hbm, peak_kind = peaks()
 
-    def bytes_model(counts, storage):
-        rec = 896.0 if storage == "f32" else 448.0
-        s_all = counts[:, 0].astype(np.float64)
-        s_occ = counts[:, 1].astype(np.float64)
-        fwd = (s_all * 32 + s_occ * rec).sum() + 20.0 * n_rays
-        bwd = (s_all[valid] * 32 + s_occ[valid] * (rec + 1792.0)).sum() + 32.0 * valid.sum() \
-            + 4.0 * n_rays
-        return fwd, bwd, float(s_all.mean()), float(s_occ.mean())
-
-    fwd_b, bwd_b, s_all, s_occ = bytes_model(main["counts"], args.storage)
+    fwd_b, bwd_b, s_all, s_occ = bytes_model(main["counts"], args.storage, valid)
     fwd_ms, bwd_ms = statistics.mean(main["fwd_ms"]), statistics.mean(main["bwd_ms"])
     dom = "backward_grid" if bwd_ms >= fwd_ms else "forward"
     dom_b, dom_ms = (bwd_b, bwd_ms) if dom == "backward_grid" else (fwd_b, fwd_ms)
     achieved = dom_b / (dom_ms / 1e3) / 1e9
     step_roof = (fwd_b + bwd_b) / (hbm * 1e9) * 1e3   # ms per step at the HBM roof
-    fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage)
+    fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage, valid)
 
     traffic = measured_traffic(dom, "room256", args.storage)
     if traffic:
@@ -355,12 +361,15 @@ def run_ours(args):
         "kernels_ms": {"forward": fwd_ms, "backward_grid": bwd_ms},
         "launch_config": {"autotuned": not args.no_tune, args.storage: main["launch_config"],
                           other_storage: other["launch_config"]},
+        "tuning_trials": main["tuning_trials"],
         "kernel_source_sha": kernel_source_sha(),
     }
     if not args.no_tracking:
         line["tracking"] = run_tracking(args, world, rank, barrier)
     if not args.no_batch:
         line["batched"] = run_batch_bench(args, barrier)
+    if not args.no_large:
+        line["large"] = run_large_bench(args, barrier)
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(sc, cams_np, rgb_np, depth_np, opts, args.cpu_seconds)
     if rank == 0:
@@ -579,6 +588,85 @@ def run_batch_bench(args, barrier):
     return out
 
 
+def run_large_bench(args, barrier):
+    """The large mapping workload: a 1024^3 multi-room house (~2% allocated),
+    BF16 storage, 16 keyframes of 1200x680 (f = 600), step 0.5 voxel, up to
+    2048 samples per ray; one step = forward + adjoint over all 13 M rays,
+    per-ray transmittance recomputed in the adjoint (only C, D and the final
+    T of each ray are kept between the two launches)."""
+    import torch
+
+    from paper_2307_03404_b300 import plx, scenes
+
+    R, occ, npr, seed = scenes.WORKLOADS["house1024"]
+    t = time.time()
+    sc = scenes.house_scene(R, occ, npr, seed, device="cuda")
+    cams_np = scenes.house_cameras(sc, 16, seed + 1, 1200, 680, 600.0)
+    rgb_t, depth_t = scenes.sensor_frames_torch(sc, cams_np, seed + 2, device="cuda")
+    log(f"[bench] house1024 scene ({sc.grid.n_alloc} allocated) + 16 frames in "
+        f"{time.time() - t:.1f}s")
+    storage = "bf16"
+    o = plx.opts_from_dict(dict(step=0.5 * float(sc.grid.h[0]), lambda_d=1.0, depth_is_z=True,
+                                max_samples=2048))
+    cams = plx.CameraSet(cams_np)
+    n_rays = int(rgb_t.shape[0])
+    grid = plx.Grid.from_scene(sc.grid, storage)
+    n_alloc = grid.n_alloc
+    del sc
+    tuned = None
+    if not args.no_tune:
+        from paper_2307_03404_b300 import autotune
+
+        tuned = autotune.tune_mapping(grid, cams, o, rgb_t, depth_t, reps=1,
+                                      cache=os.path.join("/tmp", f"plx_tuning_{os.getpid()}.json"))
+    fw = plx.render_forward(grid, cams, o)
+    grad = torch.zeros(n_alloc, plx.GRAD_STRIDE, device="cuda")
+    loss = torch.empty(2, device="cuda", dtype=torch.float64)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(ev):
+        grad.zero_()
+        ev[0].record()
+        plx.render_forward(grid, cams, o, out=fw)
+        ev[1].record()
+        plx.render_backward_grid(grid, cams, o, rgb_t, depth_t, fw["rgb"], fw["depth"],
+                                 grad=grad, loss=loss)
+        ev[2].record()
+
+    K = max(2, args.steps // 2)
+    for _ in range(args.warmup):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    barrier()
+    E = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for e in E:
+        flush.fill_(1)
+        step(e)
+    barrier()
+    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in E)
+    bwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in E)
+    step_ms = fwd_ms + bwd_ms
+    counts = plx.render_forward(grid, cams, o, counts=True)["counts"].cpu().numpy()
+    d = depth_t.cpu().numpy()
+    valid = np.isfinite(d) & (d > 0)
+    fwd_b, bwd_b, s_all, s_occ = bytes_model(counts, storage, valid)
+    hbm, peak_kind = peaks()
+    achieved = bwd_b / (bwd_ms / 1e3) / 1e9
+    out = {"workload": f"house1024: 1024^3 grid, {n_alloc} allocated "
+                       f"({n_alloc / 1024 ** 3:.2%}), {storage} storage, 16 x 1200x680 keyframes "
+                       f"({n_rays} rays), step 0.5 voxel, <= 2048 samples per ray",
+           "value": n_rays / (step_ms / 1e3), "unit": "rays/s", "ms_per_step": step_ms,
+           "kernels_ms": {"forward": fwd_ms, "backward_grid": bwd_ms},
+           "roofline": {"bound": "hbm", "kernel": "backward_grid", "achieved": achieved,
+                        "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_launch": bwd_b,
+                        "step_frac": (fwd_b + bwd_b) / (hbm * 1e9) * 1e3 / step_ms,
+                        "S_all_mean": s_all, "S_occ_mean": s_occ},
+           "loss": loss.cpu().tolist(), "launch_config": grid.get_config(),
+           "autotuned": tuned is not None, "steps": K}
+    grid.close()
+    return out
+
+
 # ---------------------------------------------------------- CPU baselines
 def cpu_baseline(sc, cams, rgb_np, depth_np, opts, seconds):
     """The FP64 oracle (as it stands) on seeded chunks of 2048 of the workload's
@@ -663,6 +751,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-rays-per-step", type=int, default=512)
     args = ap.parse_args()

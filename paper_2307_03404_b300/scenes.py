@@ -343,12 +343,160 @@ def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 
     return Scene(grid, prims, room_lo, room_hi)
 
 
+def _house_prims(rng, room_lo, room_hi, n):
+    """Two partition walls (x = 0 and z = 0, 0.12 m thick) with a door each,
+    as boxes, then ``n`` random spheres and boxes of 0.1-0.4 m half-size."""
+    prims = []
+    floor, ceil = room_lo[1], room_hi[1]
+    door_h, door_w, t = 2.1, 1.0, 0.06
+    grey = np.array([0.7, 0.7, 0.68])
+    for axis in (0, 2):  # wall normal along x, then along z
+        other = 2 - axis
+        lo_o, hi_o = room_lo[other], room_hi[other]
+        d = rng.uniform(lo_o + 1.5, hi_o - 1.5)  # door centre along the wall
+        pieces = [(lo_o, d - door_w / 2, floor, ceil), (d + door_w / 2, hi_o, floor, ceil),
+                  (d - door_w / 2, d + door_w / 2, floor + door_h, ceil)]
+        for a0, a1, y0, y1 in pieces:
+            c = np.zeros(3)
+            half = np.zeros(3)
+            c[axis], half[axis] = 0.0, t
+            c[other], half[other] = 0.5 * (a0 + a1), 0.5 * (a1 - a0)
+            c[1], half[1] = 0.5 * (y0 + y1), 0.5 * (y1 - y0)
+            prims.append({"kind": "box", "c": c, "half": half, "rgb": grey})
+    for i in range(n):
+        rgb = rng.uniform(0.1, 0.9, 3)
+        if i % 2 == 0:
+            r = rng.uniform(0.1, 0.4)
+            c = rng.uniform(room_lo + r, room_hi - r)
+            prims.append({"kind": "sphere", "c": c, "r": r, "rgb": rgb})
+        else:
+            half = rng.uniform(0.1, 0.4, 3)
+            c = rng.uniform(room_lo + half, room_hi - half)
+            c[1] = room_lo[1] + half[1] if rng.random() < 0.5 else c[1]
+            prims.append({"kind": "box", "c": c, "half": half, "rgb": rgb})
+    return prims
+
+
+def house_scene(R: int = 1024, occupancy: float = 0.02, n_prims: int = 200, seed: int = 1005,
+                half: float = 6.4, wall_inset_vox: float = 4.0, border: int = 2,
+                device: str = "cuda") -> Scene:
+    """Multi-room house for large grids, built with torch on ``device`` (a
+    1024^3 grid has 1.07 G vertices): the room box split into four rooms by two
+    partition walls with doors, plus ``n_prims`` random primitives. The same
+    recipe as ``room_scene`` otherwise: the vertices nearest to the surfaces
+    are allocated (threshold = the ``occupancy`` quantile of |sdf| + a seeded
+    +-0.05-voxel jitter, estimated on 16 M random vertices, so the fraction is
+    approximate), two border layers never allocated, density rising into the
+    solid, per-surface SH plus per-vertex noise.
+    """
+    import torch
+
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    lo = np.full(3, -half)
+    hi = np.full(3, half)
+    h = (hi - lo) / (R - 1)
+    hm = float(h.min())
+    room_lo = lo + wall_inset_vox * h
+    room_hi = hi - wall_inset_vox * h
+    prims = _house_prims(rng, room_lo, room_hi, n_prims)
+    f32 = torch.float32
+    ax = [torch.linspace(lo[a], hi[a], R, device=device, dtype=torch.float64).to(f32)
+          for a in range(3)]
+    walls = []
+    for a in range(3):
+        lo_d, hi_d = ax[a] - float(room_lo[a]), float(room_hi[a]) - ax[a]
+        walls.append((torch.minimum(lo_d, hi_d), (hi_d < lo_d).to(torch.uint8)))
+    (wx, sx), (wy, sy), (wz, sz) = walls
+    s = torch.empty((R, R, R), dtype=f32, device=device)
+    ids = torch.empty((R, R, R), dtype=torch.uint8, device=device)
+    for z0 in range(0, R, 64):
+        z1 = min(R, z0 + 64)
+        sl = torch.minimum(wy[:, None], wx[None, :])
+        idl = torch.where(wy[:, None] <= wx[None, :], 2 + sy[:, None], 0 + sx[None, :])
+        zs = wz[z0:z1, None, None]
+        zsel = zs <= sl[None]
+        s[z0:z1] = torch.where(zsel, zs, sl[None])
+        ids[z0:z1] = torch.where(zsel, (4 + sz[z0:z1])[:, None, None], idl[None])
+    for i, p in enumerate(prims):
+        ext = _prim_extent(p) + 12 * h
+        i0 = np.clip(np.floor((p["c"] - ext - lo) / h).astype(int), 0, R - 1)
+        i1 = np.clip(np.ceil((p["c"] + ext - lo) / h).astype(int) + 1, 0, R)
+        X, Yv, Z = ax[0][i0[0]:i1[0]], ax[1][i0[1]:i1[1]], ax[2][i0[2]:i1[2]]
+        c = [float(v) for v in p["c"]]
+        if p["kind"] == "sphere":
+            d = torch.sqrt((Z - c[2])[:, None, None] ** 2 + (Yv - c[1])[None, :, None] ** 2
+                           + (X - c[0])[None, None, :] ** 2) - float(p["r"])
+        else:
+            hf = [float(v) for v in p["half"]]
+            qx, qy, qz = (X - c[0]).abs() - hf[0], (Yv - c[1]).abs() - hf[1], (Z - c[2]).abs() - hf[2]
+            out = torch.sqrt(qz.clamp(min=0)[:, None, None] ** 2 + qy.clamp(min=0)[None, :, None] ** 2
+                             + qx.clamp(min=0)[None, None, :] ** 2)
+            inside = torch.maximum(torch.maximum(qz[:, None, None], qy[None, :, None]),
+                                   qx[None, None, :]).clamp(max=0)
+            d = out + inside
+        sub = s[i0[2]:i1[2], i0[1]:i1[1], i0[0]:i1[0]]
+        isub = ids[i0[2]:i1[2], i0[1]:i1[1], i0[0]:i1[0]]
+        closer = d < sub
+        sub[closer] = d[closer]
+        isub[closer] = 6 + i
+    key = s.abs()
+    key += (torch.rand((R, R, R), generator=gen, device=device, dtype=f32) - 0.5) * (0.1 * hm)
+    b = border
+    for sl_ in (np.s_[:b], np.s_[R - b:]):
+        key[sl_] = float("inf")
+        key[:, sl_] = float("inf")
+        key[:, :, sl_] = float("inf")
+    pick = torch.randint(0, R ** 3, (min(R ** 3, 1 << 24),), generator=gen, device=device)
+    sample = key.reshape(-1)[pick]
+    k = max(1, int(round(occupancy * sample.numel())))
+    w = float(torch.kthvalue(sample, k).values)
+    mask = (key <= w).reshape(-1)
+    del key
+    n = int(mask.sum())
+    links = torch.full((R ** 3,), -1, dtype=torch.int32, device=device)
+    links[mask] = torch.arange(n, dtype=torch.int32, device=device)
+    sv = s.reshape(-1)[mask].double()
+    surf = ids.reshape(-1)[mask].long()
+    del s, ids
+    wmax = max(float(sv.abs().max()), hm)
+    density = ((0.6 / hm) * (0.5 - 0.6 * sv / wmax)
+               + (0.05 / hm) * torch.randn(n, generator=gen, device=device, dtype=torch.float64))
+    base = torch.from_numpy((0.28 * rng.standard_normal((6 + len(prims), N_SH))).astype(np.float32))
+    sh = torch.randn((n, N_SH), generator=gen, device=device, dtype=f32) * 0.1 + base.to(device)[surf]
+    grid = Grid((R, R, R), lo, hi, links.reshape(R, R, R).cpu().numpy(),
+                density.float().cpu().numpy(), sh.cpu().numpy())
+    return Scene(grid, prims, room_lo, room_hi)
+
+
 def _free_space(scene: Scene, P):
     P = np.atleast_2d(P)
     d = np.minimum((P - scene.room_lo).min(axis=-1), (scene.room_hi - P).min(axis=-1))
     for p in scene.prims:
         d = np.minimum(d, _prim_sdf(P, p))
     return d
+
+
+def house_cameras(scene: Scene, n: int, seed: int, width: int = 1200, height: int = 680,
+                  f: float = 600.0, clearance: float = 0.5) -> List[Camera]:
+    """``n`` keyframes spread over the rooms of a house: each at a random
+    free-space point of the lower half, looking horizontally in a random
+    direction with a slight downward pitch."""
+    rng = np.random.default_rng(seed)
+    span = scene.room_hi - scene.room_lo
+    cams = []
+    while len(cams) < n:
+        p = rng.uniform(scene.room_lo + 0.1 * span, scene.room_hi - 0.1 * span)
+        p[1] = rng.uniform(scene.room_lo[1] + 0.1 * span[1], scene.room_lo[1] + 0.5 * span[1])
+        if _free_space(scene, p)[0] <= clearance:
+            continue
+        yaw = rng.uniform(0.0, 2.0 * np.pi)
+        pitch = np.deg2rad(rng.uniform(-20, 0))
+        look = np.array([np.cos(pitch) * np.cos(yaw), np.sin(pitch), np.cos(pitch) * np.sin(yaw)])
+        cams.append(Camera(f, f, width / 2.0 - 0.5, height / 2.0 - 0.5, width, height,
+                           look_at(p, p + look)))
+    return cams
 
 
 def room_cameras(scene: Scene, n: int, seed: int, width: int = 640, height: int = 480,
@@ -454,6 +602,70 @@ def sensor_frames(scene: Scene, cams: Sequence[Camera], seed: int, depth_noise: 
     return np.concatenate(rgbs), np.concatenate(depths)
 
 
+def sensor_frames_torch(scene: Scene, cams: Sequence[Camera], seed: int, device: str = "cuda",
+                        depth_noise: float = 0.01, missing: float = 0.02):
+    """``sensor_frames`` computed with torch on ``device`` (same sensor model;
+    the noise comes from a torch generator seeded with ``seed``), for frames
+    too many or too large for numpy."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    f64 = torch.float64
+    wall_rgb = torch.tensor([[0.8, 0.75, 0.7], [0.6, 0.65, 0.7], [0.5, 0.5, 0.45]],
+                            dtype=f64, device=device)
+    rlo = torch.tensor(scene.room_lo, dtype=f64, device=device)
+    rhi = torch.tensor(scene.room_hi, dtype=f64, device=device)
+    rgbs, depths = [], []
+    for cam in cams:
+        W, H = int(cam.width), int(cam.height)
+        v, u = torch.meshgrid(torch.arange(H, device=device, dtype=f64) + 0.5,
+                              torch.arange(W, device=device, dtype=f64) + 0.5, indexing="ij")
+        dc = torch.stack([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, torch.ones_like(u)], -1)
+        dc = dc.reshape(-1, 3)
+        zlen = dc.norm(dim=-1)
+        T = torch.tensor(np.asarray(cam.T_wc, np.float64).reshape(3, 4), device=device)
+        d = (dc @ T[:, :3].T) / zlen[:, None]
+        o = T[:, 3]
+        ta = (rlo - o) / d
+        tb = (rhi - o) / d
+        tfar = torch.maximum(ta, tb)
+        tfar = torch.where(torch.isfinite(tfar), tfar, torch.full_like(tfar, float("inf")))
+        t_best, axis = tfar.min(dim=-1)
+        col = wall_rgb[axis]
+        for p in scene.prims:
+            c = torch.tensor(p["c"], dtype=f64, device=device)
+            if p["kind"] == "sphere":
+                oc = o - c
+                bq = d @ oc
+                cq = oc @ oc - p["r"] ** 2
+                disc = bq * bq - cq
+                th = -bq - torch.sqrt(disc.clamp(min=0))
+                hit = (disc > 0) & (th > 1e-6)
+            else:
+                hf = torch.tensor(p["half"], dtype=f64, device=device)
+                t1 = (c - hf - o) / d
+                t2 = (c + hf - o) / d
+                tn = torch.nan_to_num(torch.minimum(t1, t2), nan=-float("inf")).max(dim=-1).values
+                tf = torch.nan_to_num(torch.maximum(t1, t2), nan=float("inf")).min(dim=-1).values
+                th = tn
+                hit = (tf > tn) & (tn > 1e-6)
+            closer = hit & (th < t_best)
+            t_best = torch.where(closer, th, t_best)
+            col = torch.where(closer[:, None], torch.tensor(p["rgb"], dtype=f64, device=device), col)
+        X = o + t_best[:, None] * d
+        pattern = 0.5 + 0.5 * torch.sin(7.0 * X[:, 0]) * torch.cos(5.0 * X[:, 2] + 3.0 * X[:, 1])
+        noise = torch.randn((W * H, 3), generator=gen, device=device, dtype=f64)
+        rgb = (col * (0.7 + 0.3 * pattern[:, None]) + 0.01 * noise).clamp(0.0, 1.0)
+        z = t_best / zlen
+        z = z + depth_noise * z * z * torch.randn(W * H, generator=gen, device=device, dtype=f64)
+        z = torch.where(torch.rand(W * H, generator=gen, device=device, dtype=f64) < missing,
+                        torch.zeros_like(z), z)
+        rgbs.append(rgb.float())
+        depths.append(z.float())
+    return torch.cat(rgbs), torch.cat(depths)
+
+
 def mixed_resolution_cameras(scene: Scene, n: int, seed: int,
                              sizes=((320, 240), (640, 480), (848, 480), (1200, 680))):
     """``n`` keyframes whose resolution is drawn uniformly from ``sizes``,
@@ -474,5 +686,5 @@ WORKLOADS = {
     "room256": (256, 0.10, 20, 1002),
     "room512": (512, 0.05, 20, 1003),
     "room512mix": (512, 0.05, 20, 1004),
-    "room1024": (1024, 0.02, 200, 1005),
+    "house1024": (1024, 0.02, 200, 1005),   # house_scene: multi-room, 12.8 m
 }
