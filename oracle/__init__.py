@@ -92,7 +92,9 @@ def _load():
     lib.orc_pixel_ray.restype = C.c_int
     lib.orc_se3_exp.argtypes = [P, P]
     lib.orc_pose_step.argtypes = [P, P, C.c_double, P, P]
+    lib.orc_grow.argtypes = [P, P, P, P, C.c_int64, P, C.c_int32, P, C.c_int32, C.c_double]
     lib.orc_pose_step.restype = C.c_int
+    lib.orc_grow.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -230,6 +232,33 @@ def pose_jacobian(grid, cams, opts, rgb_t, depth_t, rays=None):
     loss = lib.orc_pose_jacobian(*p.args(), _ptr(rgb_t), _ptr(depth_t), _ptr(J), _ptr(r),
                                  _ptr(H), _ptr(b), C.byref(M))
     return SimpleNamespace(J=J, resid=r, H=H, b=b, loss=float(loss), M=int(M.value))
+
+
+def grow(res, lo, hi, links, n_alloc, cams, depth, band, depth_is_z=True):
+    """Grid growth from observed depth (Sec. 6.1's dynamic grid): returns
+    (new links [res_z, res_y, res_x] int32, vertices added). ``depth`` holds
+    every pixel of every camera, camera after camera, row-major (float32, as
+    a sensor gives it); a pixel whose depth is not positive and finite adds
+    nothing."""
+    lib = _load()
+    links = np.array(links, dtype=np.int32, copy=True, order="C")
+    r = np.array([int(v) for v in res], np.int32)
+    lo_, hi_ = _f64(lo), _f64(hi)
+    cams = list(cams)
+    oc = (OrcCamera * len(cams))()
+    for i, c in enumerate(cams):
+        oc[i].fx, oc[i].fy, oc[i].cx, oc[i].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        oc[i].width, oc[i].height = int(c.width), int(c.height)
+        oc[i].T_wc[:] = [float(v) for v in np.asarray(c.T_wc, dtype=np.float64).reshape(12)]
+    d = np.ascontiguousarray(depth, dtype=np.float32)
+    if d.shape[0] != sum(int(c.width) * int(c.height) for c in cams):
+        raise ValueError("depth must hold every pixel of every camera")
+    added = lib.orc_grow(_ptr(r), _ptr(lo_), _ptr(hi_), _ptr(links), C.c_int64(int(n_alloc)), oc,
+                         C.c_int32(len(cams)), _ptr(d), C.c_int32(int(bool(depth_is_z))),
+                         C.c_double(float(band)))
+    if added < 0:
+        raise MemoryError("orc_grow")
+    return links, int(added)
 
 
 def pixel_ray(grid, cam, pixel, near=0.0):

@@ -28,7 +28,10 @@
  *     turned into a ray distance by multiplying with |d_c|;
  *   - the loss gradient of Eq. 7 is d L_g / d D (the paper prints L_p);
  *   - the pose is camera-to-world, perturbed on the left in the world frame,
- *     T <- exp(xi^) T with xi = (rho, phi), translation first.
+ *     T <- exp(xi^) T with xi = (rho, phi), translation first;
+ *   - the dynamic grid grows by allocating every vertex within a band (in
+ *     grid units, per axis) of each back-projected depth point, new vertices
+ *     numbered after the existing ones in link order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -617,4 +620,68 @@ int orc_pose_step(const double H[36], const double b[6], double damping,
   memcpy(T_wc, Tn, sizeof(Tn));
   if (xi_out) memcpy(xi_out, xi, sizeof(xi));
   return 0;
+}
+
+/* ------------------------------------------------------- grid growth */
+/* Sec. 6.1 ("a dynamic voxel grid"; how it grows is not given). Reading:
+ * every valid depth pixel of the cameras is lifted to its surface point
+ * X = o + s R d_c (s = z for a z-depth, z / |d_c| for a ray distance), and
+ * every vertex whose grid coordinates lie within `band` of X's on each axis
+ * (|i - (X - lo) / h| <= band) is allocated if it was not. Vertices that were
+ * not allocated before get the numbers n_alloc, n_alloc + 1, ... in link
+ * order (x fastest, then y, then z). depth[] holds the cameras' pixels one
+ * camera after another, row-major. Returns the number of vertices added;
+ * links is updated in place. */
+int64_t orc_grow(const int32_t res[3], const double lo[3], const double hi[3],
+                 int32_t *links, int64_t n_alloc, const orc_camera *cams,
+                 int32_t n_cams, const float *depth, int32_t depth_is_z,
+                 double band) {
+  const int64_t nv = (int64_t)res[0] * res[1] * res[2];
+  unsigned char *mark = (unsigned char *)calloc((size_t)nv, 1);
+  if (!mark) return -1;
+  double h[3];
+  for (int a = 0; a < 3; ++a) h[a] = (hi[a] - lo[a]) / (double)(res[a] - 1);
+  int64_t row = 0;
+  for (int c = 0; c < n_cams; ++c) {
+    const orc_camera *cam = &cams[c];
+    const double *T = cam->T_wc;
+    for (int v = 0; v < cam->height; ++v) {
+      for (int u = 0; u < cam->width; ++u, ++row) {
+        const double z = (double)depth[row];
+        if (!(isfinite(z) && z > 0.0)) continue;
+        const double dc0 = (u + 0.5 - cam->cx) / cam->fx;
+        const double dc1 = (v + 0.5 - cam->cy) / cam->fy;
+        const double dc2 = 1.0;
+        const double s =
+            depth_is_z ? z : z / sqrt(dc0 * dc0 + dc1 * dc1 + dc2 * dc2);
+        int64_t i0[3], i1[3];
+        int empty = 0;
+        for (int a = 0; a < 3; ++a) {
+          const double w = T[4 * a + 0] * dc0 + T[4 * a + 1] * dc1 + T[4 * a + 2] * dc2;
+          const double X = T[4 * a + 3] + s * w;
+          const double gc = (X - lo[a]) / h[a];
+          double first = ceil(gc - band), last = floor(gc + band);
+          if (first < 0.0) first = 0.0;
+          if (last > (double)(res[a] - 1)) last = (double)(res[a] - 1);
+          if (first > last) { empty = 1; break; }
+          i0[a] = (int64_t)first;
+          i1[a] = (int64_t)last;
+        }
+        if (empty) continue;
+        for (int64_t iz = i0[2]; iz <= i1[2]; ++iz)
+          for (int64_t iy = i0[1]; iy <= i1[1]; ++iy)
+            for (int64_t ix = i0[0]; ix <= i1[0]; ++ix)
+              mark[(iz * res[1] + iy) * res[0] + ix] = 1;
+      }
+    }
+  }
+  int64_t added = 0;
+  for (int64_t i = 0; i < nv; ++i) {
+    if (mark[i] && links[i] < 0) {
+      links[i] = (int32_t)(n_alloc + added);
+      ++added;
+    }
+  }
+  free(mark);
+  return added;
 }
