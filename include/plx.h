@@ -267,6 +267,8 @@ plx_status plx_pose_step(const double *JtWJ, const double *JtWr, double damping,
 /* Sec. 5.4 (RMSProp for the mapping). One RMSProp step on every stored grid
  * value, in place, from the gradient left by plx_render_backward_grid:
  *   v <- alpha v + (1 - alpha) g^2,  value <- value - lr g / (sqrt(v) + eps)
+ * with lr = lr_density for the density and lr_sh for the 27 SH values (the
+ * two differ by orders of magnitude in scale; the paper gives no rates),
  * computed in FP32 and stored in the grid's storage format (16-bit formats
  * round to nearest even).
  *   grad   DEVICE float [n_alloc][PLX_GRAD_STRIDE], slots 0..27; set to zero
@@ -274,9 +276,9 @@ plx_status plx_pose_step(const double *JtWJ, const double *JtWr, double damping,
  *   state  DEVICE float [n_alloc][PLX_GRAD_STRIDE]: the running v, zeroed by
  *          the caller before the first step
  * Asynchronous; graph-capturable. Errors: PLX_EINVAL. */
-plx_status plx_grid_rmsprop(plx_grid *grid, float *grad, float *state, float lr,
-                            float alpha, float eps, int32_t zero_grad,
-                            void *stream);
+plx_status plx_grid_rmsprop(plx_grid *grid, float *grad, float *state,
+                            float lr_density, float lr_sh, float alpha,
+                            float eps, int32_t zero_grad, void *stream);
 
 /* Sec. 5.3-5.4 (tracking by random rays of the current image, Adam). One
  * iteration on camera `cam`: n_rays pixels drawn from the frame with the
@@ -301,6 +303,34 @@ plx_status plx_track_adam_step(const plx_grid *grid, const plx_cameras *cams,
                                double lr, double beta1, double beta2,
                                double eps, double *JtWJ, double *JtWr,
                                double *loss, void *stream);
+
+/* Sec. 6.1 (the paper maps into "a dynamic voxel grid" and does not say how
+ * it grows). Growth from observed depth, on the caller's link array: every
+ * pixel whose depth is positive and finite is lifted to its surface point
+ *   X = o + s R d_c,  d_c = ((u + 1/2 - cx) / fx, (v + 1/2 - cy) / fy, 1),
+ *   s = z (depth_is_z != 0, z-depth) or z / |d_c| (ray distance),
+ * and every vertex i with |i_a - (X_a - lo_a) / h_a| <= band on each axis a
+ * is allocated if it was not. The new vertices get the numbers n_alloc,
+ * n_alloc + 1, ... in link order (x fastest, then y, then z), whatever the
+ * order in which pixels run. The per-pixel arithmetic is FP64, each
+ * operation rounded once, in the order written above.
+ *   desc   HOST: res, lo, hi and n_alloc (the current count); storage unused
+ *   links  DEVICE int32 [res_z][res_y][res_x], -1 or 0 .. n_alloc-1 (the value
+ *          -2 is reserved); updated in place
+ *   cams   intrinsics HOST, poses DEVICE (camera-to-world)
+ *   depth  DEVICE float [sum of W*H]: every pixel of every camera, camera
+ *          after camera, row-major
+ *   band   0 .. 16 (grid units)
+ *   n_new  DEVICE int64 [1]: vertices added, or -1 if n_alloc + added would
+ *          exceed INT32_MAX (then links is left as it was)
+ * Asynchronous (uses stream-ordered scratch of 8 bytes per 4096 vertices).
+ * A grid handle built on the old links does not see the change: create a new
+ * one with the grown links and values. Errors: PLX_EINVAL, PLX_ENOMEM,
+ * PLX_ECUDA (links may then hold -2 marks). */
+plx_status plx_grid_grow(const plx_grid_desc *desc, int32_t *links,
+                         const plx_cameras *cams, const float *depth,
+                         int32_t depth_is_z, double band, int64_t *n_new,
+                         void *stream);
 
 /* Launch choices of a grid's kernels (the paper has none; they do not change
  * any result). block_shift: the empty-space map marks blocks of

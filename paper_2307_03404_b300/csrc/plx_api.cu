@@ -24,8 +24,9 @@ void launch_pose_step(const double* H, const double* b, double damping, double* 
                       double* xi_out, int32_t* status, cudaStream_t s);
 int pose_kernel_blocks_per_sm(int store, int minb);
 int batch_kernel_blocks_per_sm(int store, int minb);
-void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, float lr,
-                    float alpha, float eps, int zero_grad, int num_sms, cudaStream_t s);
+void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, float lr_density,
+                    float lr_sh, float alpha, float eps, int zero_grad, int num_sms,
+                    cudaStream_t s);
 void launch_adam_pose(const double* JtWr, double* state, double* pose, double lr, double b1,
                       double b2, double eps, cudaStream_t s);
 void launch_batch(int store, int minb, const Common& P, int n_track, const float* rgb_t,
@@ -624,18 +625,60 @@ extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cam
 }
 
 // ------------------------------------------------------------ optimisers
-extern "C" plx_status plx_grid_rmsprop(plx_grid* g, float* grad, float* state, float lr,
-                                       float alpha, float eps, int32_t zero_grad, void* stream) {
+namespace plx {
+plx_status grow_impl(const plx_grid_desc* d, int32_t* links, const plx_cameras* cams,
+                     const float* depth, int32_t depth_is_z, double band, int64_t* n_new,
+                     cudaStream_t s, const char** why);
+}
+
+extern "C" plx_status plx_grid_grow(const plx_grid_desc* d, int32_t* links,
+                                    const plx_cameras* cams, const float* depth,
+                                    int32_t depth_is_z, double band, int64_t* n_new,
+                                    void* stream) {
+  if (!d || !links || !cams || !n_new) return fail(PLX_EINVAL, "grid_grow: null argument");
+  for (int a = 0; a < 3; ++a) {
+    if (d->res[a] < 2 || d->res[a] > 65536)
+      return fail(PLX_EINVAL, "grid_grow: res[%d] = %d out of [2, 65536]", a, d->res[a]);
+    if (!(d->hi[a] > d->lo[a]) || !std::isfinite(d->lo[a]) || !std::isfinite(d->hi[a]))
+      return fail(PLX_EINVAL, "grid_grow: need lo < hi on axis %d", a);
+  }
+  if (d->n_alloc < 0 || d->n_alloc > INT32_MAX)
+    return fail(PLX_EINVAL, "grid_grow: n_alloc %lld out of range", (long long)d->n_alloc);
+  if (!(band >= 0.0 && band <= 16.0)) return fail(PLX_EINVAL, "grid_grow: band outside [0, 16]");
+  if (cams->n_cams < 1 || cams->n_cams > PLX_MAX_CAMERAS)
+    return fail(PLX_EINVAL, "grid_grow: n_cams %d out of [1, %d]", cams->n_cams, PLX_MAX_CAMERAS);
+  if (!cams->intr || !cams->poses) return fail(PLX_EINVAL, "grid_grow: null intrinsics or poses");
+  int64_t rows = 0;
+  for (int c = 0; c < cams->n_cams; ++c) {
+    const plx_intrinsics& in = cams->intr[c];
+    if (in.width < 1 || in.height < 1 || (int64_t)in.width * in.height > INT32_MAX)
+      return fail(PLX_EINVAL, "grid_grow: camera %d has a bad image size", c);
+    if (!(std::isfinite(in.fx) && std::isfinite(in.fy) && in.fx != 0.0 && in.fy != 0.0 &&
+          std::isfinite(in.cx) && std::isfinite(in.cy)))
+      return fail(PLX_EINVAL, "grid_grow: camera %d has bad intrinsics", c);
+    rows += (int64_t)in.width * in.height;
+  }
+  if (!depth) return fail(PLX_EINVAL, "grid_grow: null depth");
+  const char* why = "";
+  const plx_status st = grow_impl(d, links, cams, depth, depth_is_z, band, n_new,
+                                  (cudaStream_t)stream, &why);
+  if (st != PLX_OK) return fail(st, "grid_grow: %s", why);
+  return PLX_OK;
+}
+
+extern "C" plx_status plx_grid_rmsprop(plx_grid* g, float* grad, float* state, float lr_density,
+                                       float lr_sh, float alpha, float eps, int32_t zero_grad,
+                                       void* stream) {
   const char* what = "grid_rmsprop";
   if (!g) return fail(PLX_EINVAL, "%s: null grid", what);
   if (g->desc.n_alloc == 0) return PLX_OK;
   if (!grad || !state || reinterpret_cast<uintptr_t>(grad) % 16 != 0 ||
       reinterpret_cast<uintptr_t>(state) % 16 != 0)
     return fail(PLX_EINVAL, "%s: grad and state must be non-null and 16-byte aligned", what);
-  if (!(lr >= 0.f) || !(alpha >= 0.f && alpha <= 1.f) || !(eps > 0.f))
-    return fail(PLX_EINVAL, "%s: need lr >= 0, 0 <= alpha <= 1, eps > 0", what);
-  launch_rmsprop(g->desc.storage, g->rec, grad, state, g->desc.n_alloc, lr, alpha, eps,
-                 zero_grad ? 1 : 0, g->num_sms, (cudaStream_t)stream);
+  if (!(lr_density >= 0.f) || !(lr_sh >= 0.f) || !(alpha >= 0.f && alpha <= 1.f) || !(eps > 0.f))
+    return fail(PLX_EINVAL, "%s: need lr_density, lr_sh >= 0, 0 <= alpha <= 1, eps > 0", what);
+  launch_rmsprop(g->desc.storage, g->rec, grad, state, g->desc.n_alloc, lr_density, lr_sh, alpha,
+                 eps, zero_grad ? 1 : 0, g->num_sms, (cudaStream_t)stream);
   return launch_check(what);
 }
 

@@ -24,8 +24,8 @@ __device__ __forceinline__ float rms_update(float x, float g, float& v, float lr
 
 template <int STORE>
 __global__ void k_rmsprop(void* __restrict__ rec, float* __restrict__ grad,
-                          float* __restrict__ state, int64_t n, float lr, float alpha, float eps,
-                          int zero_grad) {
+                          float* __restrict__ state, int64_t n, float lr_density, float lr_sh,
+                          float alpha, float eps, int zero_grad) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float4* g4 = reinterpret_cast<float4*>(grad + i * PLX_GRAD_STRIDE);
@@ -39,7 +39,8 @@ __global__ void k_rmsprop(void* __restrict__ rec, float* __restrict__ grad,
     }
     load_record<STORE>(rec, (int32_t)i, x);
 #pragma unroll
-    for (int j = 0; j < 28; ++j) x[j] = rms_update(x[j], g[j], v[j], lr, alpha, eps);
+    for (int j = 0; j < 28; ++j)
+      x[j] = rms_update(x[j], g[j], v[j], j == 0 ? lr_density : lr_sh, alpha, eps);
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       s4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
@@ -81,24 +82,25 @@ __global__ void k_rmsprop(void* __restrict__ rec, float* __restrict__ grad,
   }
 }
 
-void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, float lr,
-                    float alpha, float eps, int zero_grad, int num_sms, cudaStream_t s) {
+void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, float lr_density,
+                    float lr_sh, float alpha, float eps, int zero_grad, int num_sms,
+                    cudaStream_t s) {
   if (n <= 0) return;
   const int64_t want = (n + 255) / 256;
   const unsigned blocks = (unsigned)(want < 16 * num_sms ? want : 16 * num_sms);
   switch (store) {
     case PLX_STORE_F32:
-      k_rmsprop<PLX_STORE_F32><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr, alpha, eps, zero_grad);
+      k_rmsprop<PLX_STORE_F32><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr_density, lr_sh, alpha, eps, zero_grad);
       break;
     case PLX_STORE_BF16:
-      k_rmsprop<PLX_STORE_BF16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr, alpha, eps, zero_grad);
+      k_rmsprop<PLX_STORE_BF16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr_density, lr_sh, alpha, eps, zero_grad);
       break;
     case PLX_STORE_F16:
-      k_rmsprop<PLX_STORE_F16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr, alpha, eps, zero_grad);
+      k_rmsprop<PLX_STORE_F16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr_density, lr_sh, alpha, eps, zero_grad);
       break;
     default:
-      k_rmsprop<PLX_STORE_F32_BF16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr, alpha, eps,
-                                                           zero_grad);
+      k_rmsprop<PLX_STORE_F32_BF16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr_density, lr_sh,
+                                                           alpha, eps, zero_grad);
       break;
   }
 }

@@ -79,7 +79,7 @@ SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload"
            "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
            "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch",
            "plx_grid_rmsprop", "plx_track_adam_step", "plx_grid_get_config",
-           "plx_grid_set_config"]
+           "plx_grid_set_config", "plx_grid_grow"]
 
 
 def _load():
@@ -106,11 +106,12 @@ def _load():
         "plx_pose_step": [P, P, D, P, P, P, P],
         "plx_grid_get_config": [P, C.POINTER(LaunchConfig)],
         "plx_grid_set_config": [P, C.POINTER(LaunchConfig), P],
-        "plx_grid_rmsprop": [P, P, P, C.c_float, C.c_float, C.c_float, I32, P],
+        "plx_grid_rmsprop": [P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, P],
         "plx_track_adam_step": [P, C.POINTER(Cameras), I32, C.POINTER(RenderOpts), I32, C.c_uint64,
                                 P, P, P, D, D, D, D, P, P, P, P],
         "plx_render_batch": [P, C.POINTER(Cameras), C.POINTER(Work), I32, C.POINTER(RenderOpts),
                              P, P, P, P, P, P, P, P],
+        "plx_grid_grow": [C.POINTER(GridDesc), P, C.POINTER(Cameras), P, I32, D, P, P],
         "plx_render_backward_pose_noalloc": [C.POINTER(GridDesc), P, P, C.POINTER(Cameras), I32,
                                              C.POINTER(Rays), C.POINTER(RenderOpts), P, P, P, P,
                                              P, P],
@@ -378,10 +379,35 @@ def render_batch(grid: Grid, cams: CameraSet, work, opts, rgb_target, depth_targ
     return grad, map_loss, out[0][:n_track], out[1][:n_track], out[2][:n_track]
 
 
-def grid_rmsprop(grid: Grid, grad, state, lr, alpha=0.99, eps=1e-8, zero_grad=True, stream=None):
-    """plx_grid_rmsprop: one RMSProp step on every stored grid value, in place."""
-    _check(_lib.plx_grid_rmsprop(grid.handle, _ptr(grad), _ptr(state), float(lr), float(alpha),
-                                 float(eps), int(bool(zero_grad)), _stream(stream)))
+def grid_rmsprop(grid: Grid, grad, state, lr, alpha=0.99, eps=1e-8, zero_grad=True, stream=None,
+                 lr_density=None):
+    """plx_grid_rmsprop: one RMSProp step on every stored grid value, in place
+    (``lr`` for the SH values, ``lr_density`` for the density; the same if
+    not given)."""
+    lr_d = lr if lr_density is None else lr_density
+    _check(_lib.plx_grid_rmsprop(grid.handle, _ptr(grad), _ptr(state), float(lr_d), float(lr),
+                                 float(alpha), float(eps), int(bool(zero_grad)), _stream(stream)))
+
+
+def grid_grow(res, lo, hi, links: torch.Tensor, n_alloc: int, cams: CameraSet, depth, band,
+              depth_is_z=True, n_new=None, stream=None):
+    """Grow a link array from observed depth (``plx_grid_grow``): ``links`` (a
+    CUDA int32 tensor [R_z, R_y, R_x]) is updated in place; returns the device
+    int64 count of vertices added (-1 if the numbering would overflow int32).
+    Asynchronous; read the count to synchronise."""
+    if links.dtype != torch.int32 or not links.is_cuda or not links.is_contiguous():
+        raise ValueError("links must be a contiguous CUDA int32 tensor")
+    d = GridDesc()
+    d.res[:] = [int(v) for v in res]
+    d.lo[:] = [float(v) for v in lo]
+    d.hi[:] = [float(v) for v in hi]
+    d.n_alloc = int(n_alloc)
+    if n_new is None:
+        n_new = torch.empty(1, dtype=torch.int64, device="cuda")
+    cs = cams.struct()
+    _check(_lib.plx_grid_grow(C.byref(d), _ptr(links), C.byref(cs), _ptr(depth.contiguous()),
+                              int(bool(depth_is_z)), float(band), _ptr(n_new), _stream(stream)))
+    return n_new
 
 
 def adam_state():

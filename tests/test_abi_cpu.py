@@ -110,3 +110,26 @@ def test_argument_errors_are_reported_without_touching_the_gpu(lib):
     assert b"damping" in lib.plx_last_error()
     assert lib.plx_render_forward(None, None, None, None, None, None, None, None, None) == 1
     assert lib.plx_grid_destroy(None) == 0
+
+
+def test_grid_grow_argument_errors(lib):
+    from paper_2307_03404_b300 import plx
+
+    lib = plx._lib
+    x = (C.c_double * 16)()
+    assert lib.plx_grid_grow(None, None, None, None, 1, 1.0, None, None) == 1
+    assert b"null" in lib.plx_last_error()
+    d = plx.GridDesc()
+    d.res[:] = [4, 4, 4]
+    d.hi[:] = [1, 1, 1]
+    cams = plx.Cameras()
+    cams.n_cams = 1
+    assert lib.plx_grid_grow(C.byref(d), x, C.byref(cams), x, 1, -0.5, x, None) == 1
+    assert b"band" in lib.plx_last_error()
+    assert lib.plx_grid_grow(C.byref(d), x, C.byref(cams), x, 1, float("nan"), x, None) == 1
+    cams.n_cams = 0
+    assert lib.plx_grid_grow(C.byref(d), x, C.byref(cams), x, 1, 2.0, x, None) == 1
+    assert b"n_cams" in lib.plx_last_error()
+    d.n_alloc = -3
+    assert lib.plx_grid_grow(C.byref(d), x, C.byref(cams), x, 1, 2.0, x, None) == 1
+    assert b"n_alloc" in lib.plx_last_error()

@@ -23,11 +23,14 @@ def test_rmsprop_step_matches_oracle(storage):
     st = np.zeros((n, 32), np.float32)
     st[:, :28] = rng.uniform(0, 2, (n, 28)).astype(np.float32)
     grad, state = dev(gr), dev(st)
-    plx.grid_rmsprop(grid, grad, state, lr=0.01, alpha=0.9, eps=1e-6, zero_grad=True)
+    plx.grid_rmsprop(grid, grad, state, lr=0.01, lr_density=0.5, alpha=0.9, eps=1e-6,
+                     zero_grad=True)
     d1, s1 = grid.download()
     torch.cuda.synchronize()
     x1 = torch.cat([d1[:, None], s1], 1).cpu().numpy()
-    xr, vr = oracle.rmsprop(x0, gr[:, :28], st[:, :28], 0.01, 0.9, 1e-6)
+    lr = np.full(28, 0.01)
+    lr[0] = 0.5  # density
+    xr, vr = oracle.rmsprop(x0, gr[:, :28], st[:, :28], lr, 0.9, 1e-6)
     np.testing.assert_allclose(state.cpu().numpy()[:, :28], vr, rtol=1e-6)
     assert np.all(grad.cpu().numpy() == 0)
     if storage == "f32":
