@@ -370,6 +370,16 @@ def run_ours(args):
         line["batched"] = run_batch_bench(args, barrier)
     if not args.no_large:
         line["large"] = run_large_bench(args, barrier)
+    if not args.no_pipeline:
+        from paper_2307_03404_b300 import pipeline
+
+        t = time.time()
+        pl = pipeline.run(sc, log=log)
+        pl["wall_seconds"] = time.time() - t
+        pl["workload"] = ("room256 geometry, 300-frame 640x480 sequence (path_m long), every 10th "
+                          "frame mapped into a dynamic 256^3 grid grown from depth, every frame "
+                          "tracked (Adam, 200 iterations of 4096 random rays, one CUDA graph)")
+        line["pipeline"] = pl
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(sc, cams_np, rgb_np, depth_np, opts, args.cpu_seconds)
     if rank == 0:
@@ -752,6 +762,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-pipeline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-rays-per-step", type=int, default=512)
     args = ap.parse_args()

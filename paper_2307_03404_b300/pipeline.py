@@ -1,0 +1,282 @@
+"""The paper's two-stage method over a sequence (Sec. 5, Sec. 6.1): offline
+mapping of every k-th frame with known poses into a dynamic grid, then online
+tracking of every frame against the fixed map, with the trajectory metrics of
+Sec. 6.1 (ATE, RPE_t, RPE_r over 1 m) and the mapping metrics (L1 depth error
+and colour PSNR on random pixels of random frames).
+
+Every rendering, gradient, optimiser and growth step runs in the CUDA library;
+this module only sequences the calls, holds the device buffers and draws the
+random ray lists of the mapping steps (Sec. 5.4: mapping takes "a random set of
+sample rays from all available images").
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import plx, trajectory
+
+
+class DynamicGrid:
+    """A sparse grid that grows from observed depth (``plx_grid_grow``). The
+    link array stays on the device; after each growth the library grid is
+    rebuilt with the current values plus initial values for the new vertices
+    (density ``density0`` > 0, where the ReLU passes gradient; SH 0, colour 0.5),
+    and the RMSProp state is extended with zeros."""
+
+    def __init__(self, res, lo, hi, storage="f32", density0=0.1):
+        self.res = tuple(int(r) for r in res)
+        self.lo = np.asarray(lo, np.float64)
+        self.hi = np.asarray(hi, np.float64)
+        self.storage = storage
+        self.density0 = float(density0)
+        R = self.res
+        self.links = torch.full((R[2], R[1], R[0]), -1, dtype=torch.int32, device="cuda")
+        self.n = 0
+        self.grid = None
+        self.state = torch.zeros(0, plx.GRAD_STRIDE, device="cuda")
+
+    def grow(self, cams: plx.CameraSet, depth: torch.Tensor, band: float, depth_is_z=True) -> int:
+        n_new = int(plx.grid_grow(self.res, self.lo, self.hi, self.links, self.n, cams, depth, band,
+                                  depth_is_z=depth_is_z).item())
+        if n_new < 0:
+            raise RuntimeError("grid_grow: vertex count would exceed int32")
+        if n_new == 0 and self.grid is not None:
+            return 0
+        if self.grid is not None:
+            dens, sh = self.grid.download()
+            self.grid.close()
+        else:
+            dens = torch.empty(0, device="cuda")
+            sh = torch.empty(0, 27, device="cuda")
+        dens = torch.cat([dens, torch.full((n_new,), self.density0, device="cuda")])
+        sh = torch.cat([sh, torch.zeros(n_new, 27, device="cuda")])
+        self.state = torch.cat([self.state, torch.zeros(n_new, plx.GRAD_STRIDE, device="cuda")])
+        self.n += n_new
+        self.grid = plx.Grid(self.res, self.lo, self.hi, self.links, dens, sh, self.storage)
+        return n_new
+
+    def close(self):
+        if self.grid is not None:
+            self.grid.close()
+            self.grid = None
+
+
+@dataclasses.dataclass
+class MapConfig:
+    """RMSProp mapping; the rates decay exponentially from lr_* to lr_*_final
+    over the steps (the paper gives no schedule)."""
+    iters: int = 1000
+    rays_per_step: int = 1 << 18
+    lr_density: float = 3.0
+    lr_sh: float = 0.02
+    lr_density_final: float = 3.0
+    lr_sh_final: float = 0.02
+    alpha: float = 0.95
+    eps: float = 1e-8
+    band: float = 2.0
+    seed: int = 7
+
+
+@dataclasses.dataclass
+class TrackConfig:
+    """Adam tracking per frame; the rate decays exponentially from lr to
+    lr_final over the iterations (each captured call carries its own rate)."""
+    iters: int = 200
+    n_rays: int = 4096
+    lr: float = 1e-3
+    lr_final: float = 1e-4
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    constant_velocity: bool = True
+    seed: int = 11
+
+
+def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: torch.Tensor,
+                opts, cfg: MapConfig, log=None):
+    """Grow the grid from the keyframes' depth, then ``cfg.iters`` RMSProp
+    steps, each on ``cfg.rays_per_step`` rays drawn uniformly (with
+    replacement) from all keyframe pixels. rgb/depth hold every pixel of every
+    keyframe in camera order. Returns per-step losses (device FP64 [iters])."""
+    dg.grow(cams, depth, cfg.band, depth_is_z=bool(opts.depth_is_z))
+    sizes = torch.tensor([w * h for w, h in cams.sizes], device="cuda")
+    offs = torch.cumsum(sizes, 0) - sizes
+    total = int(sizes.sum())
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cfg.seed)
+    grad = torch.zeros(dg.n, plx.GRAD_STRIDE, device="cuda")
+    losses = torch.zeros(cfg.iters, 2, dtype=torch.float64, device="cuda")
+    fw = None
+    for it in range(cfg.iters):
+        rows = torch.randint(0, total, (cfg.rays_per_step,), generator=gen, device="cuda")
+        cam_id = (torch.searchsorted(offs, rows, right=True) - 1).to(torch.int32)
+        pix = (rows - offs[cam_id.long()]).to(torch.int32)
+        rays = (cam_id, pix)
+        rgb_t, depth_t = rgb[rows], depth[rows]
+        fw = plx.render_forward(dg.grid, cams, opts, rays=rays, out=fw)
+        plx.render_backward_grid(dg.grid, cams, opts, rgb_t, depth_t, fw["rgb"], fw["depth"],
+                                 rays=rays, grad=grad, loss=losses[it])
+        f = it / max(1, cfg.iters - 1)
+        lr_d = cfg.lr_density * (cfg.lr_density_final / cfg.lr_density) ** f
+        lr_s = cfg.lr_sh * (cfg.lr_sh_final / cfg.lr_sh) ** f
+        plx.grid_rmsprop(dg.grid, grad, dg.state, lr_s, cfg.alpha, cfg.eps, zero_grad=True,
+                         lr_density=lr_d)
+        if log and (it % 250 == 0 or it == cfg.iters - 1):
+            log(f"[map] step {it} loss {float(losses[it, 0]):.5f}")
+    return losses[:, 0]
+
+
+def mapping_metrics(grid: plx.Grid, cam_list, rgb_frames, depth_frames, opts, n_rays=100_000,
+                    n_frames=32, seed=3):
+    """L1 depth error (metres, over pixels with valid depth) and colour PSNR
+    (dB, peak 1) on random pixels of ``n_frames`` random frames (Sec. 6.1's
+    mapping metrics). The rendered depth is a ray distance; sensor z-depths
+    are compared after turning them into ray distances. rgb_frames /
+    depth_frames: [n, W*H, 3] / [n, W*H], one camera size."""
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(len(cam_list), size=min(n_frames, len(cam_list)), replace=False))
+    cam_list = [cam_list[k] for k in pick]
+    cams = plx.CameraSet(cam_list)
+    npx = int(cam_list[0].width) * int(cam_list[0].height)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    cam_id = torch.randint(0, len(cam_list), (n_rays,), generator=gen, device="cuda",
+                           dtype=torch.int32)
+    pix = torch.randint(0, npx, (n_rays,), generator=gen, device="cuda", dtype=torch.int32)
+    frame = torch.from_numpy(pick).cuda()[cam_id.long()]
+    rgb_t = rgb_frames[frame, pix.long()]
+    d = depth_frames[frame, pix.long()].double()
+    out = plx.render_forward(grid, cams, opts, rays=(cam_id, pix), state=False)
+    mse = torch.mean((out["rgb"].double() - rgb_t.double()) ** 2)
+    psnr = float(-10.0 * torch.log10(mse))
+    ok = torch.isfinite(d) & (d > 0)
+    if opts.depth_is_z:
+        par = torch.tensor([[c.fx, c.fy, c.cx, c.cy, c.width] for c in cam_list],
+                           dtype=torch.float64, device="cuda")[cam_id.long()]
+        p = pix.double()
+        u = torch.remainder(p, par[:, 4]) + 0.5
+        v = torch.div(p, par[:, 4], rounding_mode="floor") + 0.5
+        d = d * torch.sqrt(((u - par[:, 2]) / par[:, 0]) ** 2 + ((v - par[:, 3]) / par[:, 1]) ** 2
+                           + 1.0)
+    l1 = float(torch.mean(torch.abs(out["depth"].double()[ok] - d[ok])))
+    return {"l1_depth_m": l1, "psnr_db": psnr, "rays": n_rays}
+
+
+def track_sequence(grid: plx.Grid, cam_list, rgb_frames, depth_frames, opts, cfg: TrackConfig,
+                   init_pose=None, log=None):
+    """Track every frame against the fixed map: Adam on random rays of the
+    current frame (``plx_track_adam_step``), ``cfg.iters`` iterations per
+    frame captured in one CUDA graph. Frame k starts from frame k-1's estimate
+    (times the last inter-frame motion when ``constant_velocity``); frame 0
+    starts at ``init_pose`` (default: its given pose). Returns the estimated
+    poses [n, 3, 4] (FP64, numpy) and the mean milliseconds per frame."""
+    intr = cam_list[0]
+    one = plx.CameraSet([intr])
+    W, H = int(intr.width), int(intr.height)
+    rgb_buf = torch.empty(W * H, 3, device="cuda")
+    depth_buf = torch.empty(W * H, device="cuda")
+    state = plx.adam_state()
+    outs = (torch.empty(6, 6, device="cuda", dtype=torch.float64),
+            torch.empty(6, device="cuda", dtype=torch.float64),
+            torch.empty(2, device="cuda", dtype=torch.float64))
+
+    def iterations():
+        for k in range(cfg.iters):
+            lr = cfg.lr * (cfg.lr_final / cfg.lr) ** (k / max(1, cfg.iters - 1))
+            plx.track_adam_step(grid, one, 0, opts, cfg.n_rays, cfg.seed, rgb_buf, depth_buf, state,
+                                lr, cfg.beta1, cfg.beta2, cfg.eps, out=outs)
+
+    # capture once (warm-up on a side stream first, as CUDA graphs require)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        state.zero_()
+        plx.track_adam_step(grid, one, 0, opts, cfg.n_rays, cfg.seed, rgb_buf, depth_buf, state,
+                            cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, out=outs)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        iterations()
+
+    n = len(cam_list)
+    est = np.zeros((n, 3, 4))
+    est_h = np.tile(np.eye(4), (n, 1, 1))
+    first = np.asarray(cam_list[0].T_wc if init_pose is None else init_pose, np.float64)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for k in range(n):
+        if k == 0:
+            pred = first.reshape(3, 4)
+        elif cfg.constant_velocity and k >= 2:
+            motion = est_h[k - 1] @ np.linalg.inv(est_h[k - 2])
+            pred = (motion @ est_h[k - 1])[:3]
+        else:
+            pred = est[k - 1]
+        one.poses.copy_(torch.from_numpy(pred.reshape(1, 12)))
+        rgb_buf.copy_(rgb_frames[k])
+        depth_buf.copy_(depth_frames[k])
+        state.zero_()
+        start.record()
+        graph.replay()
+        end.record()
+        end.synchronize()
+        ms += start.elapsed_time(end)
+        est[k] = one.poses.reshape(3, 4).cpu().numpy()
+        est_h[k, :3] = est[k]
+        if log and k % 50 == 0:
+            log(f"[track] frame {k}")
+    return est, ms / n
+
+
+def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", depth_noise=0.0025,
+        map_cfg=None, track_cfg=None, seed=21, log=None):
+    """Whole pipeline on a synthetic room: a smooth sequence of ``n_frames``
+    640x480 RGB-D frames along the first ``span`` of a spline path (depth
+    noise N(0, (depth_noise z^2)^2), 2% of depths missing), every
+    ``map_every``-th frame mapped with its true pose into a ``res``^3 dynamic
+    grid over the scene's box, every frame tracked from the first true pose.
+    Returns a dict of metrics and timings."""
+    from . import scenes
+
+    map_cfg = map_cfg or MapConfig()
+    track_cfg = track_cfg or TrackConfig()
+    cams_np = scenes.sequence_cameras(scene, n_frames, seed, span=span)
+    rgb, depth = scenes.sensor_frames_torch(scene, cams_np, seed + 1, device="cuda",
+                                            depth_noise=depth_noise)
+    npx = cams_np[0].width * cams_np[0].height
+    rgb = rgb.reshape(n_frames, npx, 3)
+    depth = depth.reshape(n_frames, npx)
+    g = scene.grid
+    R = res or g.res[0]
+    opts = plx.opts_from_dict(dict(step=0.5 * float((g.hi[0] - g.lo[0]) / (R - 1)), lambda_d=1.0,
+                                   depth_is_z=True))
+    keys = list(range(0, n_frames, map_every))
+    kcams = plx.CameraSet([cams_np[k] for k in keys])
+    krgb = rgb[keys].reshape(-1, 3).contiguous()
+    kdepth = depth[keys].reshape(-1).contiguous()
+    dg = DynamicGrid((R, R, R), g.lo, g.hi, storage)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    losses = map_offline(dg, kcams, krgb, kdepth, opts, map_cfg, log=log)
+    torch.cuda.synchronize()
+    t_map = time.time() - t0
+    mm = mapping_metrics(dg.grid, cams_np, rgb, depth, opts)
+    gt = np.array([np.asarray(c.T_wc, np.float64).reshape(3, 4) for c in cams_np])
+    est, ms_frame = track_sequence(dg.grid, cams_np, rgb, depth, opts, track_cfg, log=log)
+    t_rpe, r_rpe = trajectory.rpe(est, gt)
+    err = np.linalg.norm(est[:, :, 3] - gt[:, :, 3], axis=1)
+    out = {"frames": n_frames, "keyframes": len(keys), "grid": f"{R}^3 dynamic, {storage}",
+           "allocated": dg.n, "map_seconds": t_map, "map_steps": map_cfg.iters,
+           "map_rays_per_step": map_cfg.rays_per_step,
+           "map_loss_first_last": [float(losses[0]), float(losses[-1])],
+           "mapping": mm, "track_ms_per_frame": ms_frame, "track_iters": track_cfg.iters,
+           "track_rays": track_cfg.n_rays,
+           "ate_m": trajectory.ate(est, gt), "rpe_t_m": t_rpe, "rpe_r_deg": r_rpe,
+           "median_err_m": float(np.median(err)), "max_err_m": float(err.max()),
+           "path_m": float(np.sum(np.linalg.norm(np.diff(gt[:, :, 3], axis=0), axis=1)))}
+    dg.close()
+    return out

@@ -499,12 +499,9 @@ def house_cameras(scene: Scene, n: int, seed: int, width: int = 1200, height: in
     return cams
 
 
-def room_cameras(scene: Scene, n: int, seed: int, width: int = 640, height: int = 480,
-                 f: float = 525.0, clearance: float = 0.5) -> List[Camera]:
-    """``n`` keyframes on a Catmull-Rom spline through six random free-space
-    points of the room, each looking along the path with a small random yaw
-    and a slight downward pitch."""
-    rng = np.random.default_rng(seed)
+def _spline_path(scene: Scene, rng, clearance: float):
+    """Catmull-Rom spline through six random free-space points of the room
+    (drawn from ``rng``): returns (spline(u) -> (position, tangent), segments)."""
     span = scene.room_hi - scene.room_lo
     pts = []
     while len(pts) < 6:
@@ -524,21 +521,69 @@ def room_cameras(scene: Scene, n: int, seed: int, width: int = 640, height: int 
                      + 3 * (-p0 + 3 * p1 - 3 * p2 + p3) * t * t)
         return pos, tan
 
+    return spline, len(pts) - 1
+
+
+def _heading(tan, yaw, pitch):
+    fwd = np.array([tan[0], 0.0, tan[2]])
+    if np.linalg.norm(fwd) < 1e-6:
+        fwd = np.array([1.0, 0.0, 0.0])
+    fwd /= np.linalg.norm(fwd)
+    cy_, sy_ = np.cos(yaw), np.sin(yaw)
+    fwd = np.array([cy_ * fwd[0] - sy_ * fwd[2], 0.0, sy_ * fwd[0] + cy_ * fwd[2]])
+    return np.cos(pitch) * fwd + np.array([0.0, np.sin(pitch), 0.0])
+
+
+def room_cameras(scene: Scene, n: int, seed: int, width: int = 640, height: int = 480,
+                 f: float = 525.0, clearance: float = 0.5) -> List[Camera]:
+    """``n`` keyframes on a Catmull-Rom spline through six random free-space
+    points of the room, each looking along the path with a small random yaw
+    and a slight downward pitch."""
+    rng = np.random.default_rng(seed)
+    spline, segs = _spline_path(scene, rng, clearance)
     cams = []
     for i in range(n):
-        u = (len(pts) - 1) * (i + 0.5) / n
+        u = segs * (i + 0.5) / n
         pos, tan = spline(u)
-        fwd = np.array([tan[0], 0.0, tan[2]])
-        if np.linalg.norm(fwd) < 1e-6:
-            fwd = np.array([1.0, 0.0, 0.0])
-        fwd /= np.linalg.norm(fwd)
         yaw = np.deg2rad(rng.uniform(-10, 10))
         pitch = np.deg2rad(rng.uniform(-15, 0))
-        cy_, sy_ = np.cos(yaw), np.sin(yaw)
-        fwd = np.array([cy_ * fwd[0] - sy_ * fwd[2], 0.0, sy_ * fwd[0] + cy_ * fwd[2]])
-        look = np.cos(pitch) * fwd + np.array([0.0, np.sin(pitch), 0.0])
+        look = _heading(tan, yaw, pitch)
         cams.append(Camera(f, f, width / 2.0 - 0.5, height / 2.0 - 0.5, width, height,
                            look_at(pos, pos + look)))
+    return cams
+
+
+def sequence_cameras(scene: Scene, n: int, seed: int, width: int = 640, height: int = 480,
+                     f: float = 525.0, clearance: float = 0.5, span: float = 1.0,
+                     smooth: float = 0.1) -> List[Camera]:
+    """A smooth camera sequence of ``n`` frames along the same kind of spline
+    (the first ``span`` of it). The heading follows the path direction,
+    low-passed (Gaussian over ``smooth`` of the sequence) so sharp bends of the
+    path turn the camera gradually, plus a slowly oscillating yaw (+-10
+    degrees) and pitch (-12..-4 degrees): consecutive frames are close in
+    pose."""
+    rng = np.random.default_rng(seed)
+    spline, segs = _spline_path(scene, rng, clearance)
+    ph = rng.uniform(0, 2 * np.pi, 2)
+    us = segs * span * np.arange(n) / max(1, n - 1) * 0.999
+    pos, yaw = [], []
+    for u in us:
+        p, tan = spline(u)
+        pos.append(p)
+        yaw.append(np.arctan2(tan[2], tan[0]) if np.hypot(tan[0], tan[2]) > 1e-6 else 0.0)
+    yaw = np.unwrap(np.array(yaw))
+    sig = max(1e-9, smooth * n)
+    k = np.arange(-int(3 * sig) - 1, int(3 * sig) + 2)
+    w = np.exp(-0.5 * (k / sig) ** 2)
+    pad = np.concatenate([np.full(len(k) // 2, yaw[0]), yaw, np.full(len(k) // 2, yaw[-1])])
+    yaw = np.convolve(pad, w / w.sum(), mode="valid")[:n]
+    cams = []
+    for i, u in enumerate(us):
+        a = yaw[i] + np.deg2rad(10.0 * np.sin(2 * np.pi * u / 3.0 + ph[0]))
+        pitch = np.deg2rad(-8.0 + 4.0 * np.sin(2 * np.pi * u / 2.0 + ph[1]))
+        look = np.array([np.cos(pitch) * np.cos(a), np.sin(pitch), np.cos(pitch) * np.sin(a)])
+        cams.append(Camera(f, f, width / 2.0 - 0.5, height / 2.0 - 0.5, width, height,
+                           look_at(pos[i], pos[i] + look)))
     return cams
 
 
