@@ -62,7 +62,7 @@ class OrcOpts(C.Structure):
         ("max_samples", C.c_int32),
         ("color_act", C.c_int32),
         ("depth_is_z", C.c_int32),
-        ("pad_", C.c_int32),
+        ("dir_term", C.c_int32),
     ]
 
 
@@ -81,6 +81,7 @@ def _load():
     lib.orc_set_threads.argtypes = [C.c_int]
     lib.orc_get_threads.restype = C.c_int
     lib.orc_sh_basis.argtypes = [P, P]
+    lib.orc_sh_basis_grad.argtypes = [P, P]
     lib.orc_trilerp.argtypes = [P, C.c_double, C.c_double, C.c_double, P, P]
     lib.orc_render.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P]
     lib.orc_render_frozen.argtypes = [P, P, C.c_int64, P, P, P, P, P, P]
@@ -162,6 +163,7 @@ class _Prepared:
         o.max_samples = int(opts.get("max_samples", 1 << 30))
         o.color_act = {"sigmoid": 0, "identity": 1}[opts.get("color_act", "sigmoid")]
         o.depth_is_z = int(bool(opts.get("depth_is_z", True)))
+        o.dir_term = int(bool(opts.get("dir_term", False)))
         self.opts = o
 
     def args(self):
@@ -294,6 +296,14 @@ def sh_basis(d):
     Y = np.zeros(9)
     _load().orc_sh_basis(_ptr(d), _ptr(Y))
     return Y
+
+
+def sh_basis_grad(d):
+    """[9, 3]: gradient of the nine SH polynomials at d (tracking-Jacobian variant)."""
+    d = _f64(d, (3,))
+    G = np.zeros((9, 3))
+    _load().orc_sh_basis_grad(_ptr(d), _ptr(G))
+    return G
 
 
 def trilerp(V, x, y, z):

@@ -65,7 +65,7 @@ typedef struct {
   int32_t max_samples;
   int32_t color_act;       /* 0 = sigmoid, 1 = identity */
   int32_t depth_is_z;      /* 1 = depth targets are sensor z-depths */
-  int32_t pad_;
+  int32_t dir_term;        /* 1 = tracking Jacobian includes dc/dd (variant) */
 } orc_opts;
 
 static int g_threads = 1;
@@ -93,6 +93,28 @@ void orc_sh_basis(const double dir[3], double Y[9]) {
   Y[6] = k20 * (3.0 * z * z - 1.0);
   Y[7] = k2 * x * z;
   Y[8] = k22 * (x * x - y * y);
+}
+
+/* Gradient of the same nine polynomials in (x, y, z), dY[k][a] = dY_k/dx_a
+ * (the view-direction term of the tracking Jacobian variant; only its
+ * component tangent to the sphere matters, and the rotation of a direction
+ * is tangent). */
+void orc_sh_basis_grad(const double dir[3], double dY[9][3]) {
+  const double pi = 3.14159265358979323846;
+  const double x = dir[0], y = dir[1], z = dir[2];
+  const double k1 = sqrt(3.0 / (4.0 * pi));
+  const double k2 = sqrt(15.0 / (4.0 * pi));
+  const double k20 = sqrt(5.0 / (16.0 * pi));
+  const double k22 = sqrt(15.0 / (16.0 * pi));
+  for (int k = 0; k < 9; ++k) dY[k][0] = dY[k][1] = dY[k][2] = 0.0;
+  dY[1][1] = k1;
+  dY[2][2] = k1;
+  dY[3][0] = k1;
+  dY[4][0] = k2 * y;  dY[4][1] = k2 * x;
+  dY[5][1] = k2 * z;  dY[5][2] = k2 * y;
+  dY[6][2] = k20 * 6.0 * z;
+  dY[7][0] = k2 * z;  dY[7][2] = k2 * x;
+  dY[8][0] = k22 * 2.0 * x;  dY[8][1] = -k22 * 2.0 * y;
 }
 
 /* ----------------------------------------------------- trilinear, App. A */
@@ -198,6 +220,7 @@ typedef struct {
   double dc_dchat[3];    /* activation derivative */
   double gsig[3];        /* d f_sigma / d p (world) */
   double gchat[3][3];    /* d chat_ch / d p (world), [ch][axis] */
+  double f_sh[3][9];     /* interpolated SH coefficients at p */
 } orc_sample;
 
 static void eval_sample(const orc_grid *g, const double p[3], const double Y[9],
@@ -241,6 +264,7 @@ static void eval_sample(const orc_grid *g, const double p[3], const double Y[9],
       for (int c = 0; c < 8; ++c)
         V[c] = s->link[c] >= 0 ? g->sh[(int64_t)s->link[c] * 27 + ch * 9 + k] : 0.0;
       orc_trilerp(V, xl[0], xl[1], xl[2], &f, gl);
+      s->f_sh[ch][k] = f;
       s->chat[ch] += Y[k] * f;
       for (int a = 0; a < 3; ++a) s->gchat[ch][a] += Y[k] * gl[a] / h[a];
     }
@@ -279,10 +303,11 @@ typedef struct {
 
 /* Colour (Eq. 1) with transmittance (Eq. 2) and expected depth (Eq. 3) of the
  * samples o + t_k d; the sample positions may be taken from another pose
- * (o_s, d_s) than the one that fixed t_k and the SH direction (the frozen-sample
- * form used to difference the pose Jacobian). */
+ * (o_s, d_s) than the one that fixed t_k, and the SH basis Y_s from another
+ * direction (the frozen-sample form used to difference the pose Jacobian). */
 static void forward_ray(const orc_grid *g, const orc_ray *r, const double *o_s,
-                        const double *d_s, const orc_opts *op, orc_fwd *out) {
+                        const double *d_s, const double *Y_s, const orc_opts *op,
+                        orc_fwd *out) {
   double tau = 0.0; /* sum_{j<i} sigma_j delta_j */
   for (int ch = 0; ch < 3; ++ch) out->C[ch] = 0.0;
   out->D = 0.0;
@@ -293,7 +318,7 @@ static void forward_ray(const orc_grid *g, const orc_ray *r, const double *o_s,
     double p[3];
     orc_sample s;
     for (int a = 0; a < 3; ++a) p[a] = o_s[a] + t * d_s[a];
-    eval_sample(g, p, r->Y, op->color_act, &s);
+    eval_sample(g, p, Y_s, op->color_act, &s);
     out->n_marched++;
     out->n_alloc += s.any_alloc;
     const double T_i = exp(-tau);
@@ -319,7 +344,7 @@ void orc_render(const orc_grid *g, const orc_camera *cams, int64_t n_rays,
     orc_fwd f;
     const orc_camera *cam = &cams[cam_id[i]];
     setup_ray(g, cam, pix[i], op, &r);
-    forward_ray(g, &r, r.o, r.d, op, &f);
+    forward_ray(g, &r, r.o, r.d, r.Y, op, &f);
     for (int ch = 0; ch < 3; ++ch) rgb[3 * i + ch] = f.C[ch];
     depth[i] = f.D;
     if (T_final) T_final[i] = f.T_final;
@@ -328,8 +353,9 @@ void orc_render(const orc_grid *g, const orc_camera *cams, int64_t n_rays,
   }
 }
 
-/* Frozen-sample forward: t_k, delta_k and the SH direction come from the
- * camera's own pose; the positions come from exp(xi^) T_wc. */
+/* Frozen-sample forward: t_k, delta_k (and, unless op->dir_term, the SH
+ * direction) come from the camera's own pose; the positions (and with
+ * op->dir_term the SH direction) come from exp(xi^) T_wc. */
 void orc_se3_exp(const double xi[6], double T[12]);
 
 void orc_render_frozen(const orc_grid *g, const orc_camera *cams, int64_t n_rays,
@@ -348,7 +374,9 @@ void orc_render_frozen(const orc_grid *g, const orc_camera *cams, int64_t n_rays
       o2[a] = E[4 * a + 0] * r.o[0] + E[4 * a + 1] * r.o[1] + E[4 * a + 2] * r.o[2] + E[4 * a + 3];
       d2[a] = E[4 * a + 0] * r.d[0] + E[4 * a + 1] * r.d[1] + E[4 * a + 2] * r.d[2];
     }
-    forward_ray(g, &r, o2, d2, op, &f);
+    double Y2[9];
+    orc_sh_basis(d2, Y2);
+    forward_ray(g, &r, o2, d2, op->dir_term ? Y2 : r.Y, op, &f);
     for (int ch = 0; ch < 3; ++ch) rgb[3 * i + ch] = f.C[ch];
     depth[i] = f.D;
   }
@@ -386,7 +414,7 @@ double orc_grad_grid(const orc_grid *g, const orc_camera *cams, int64_t n_rays,
     orc_ray r;
     orc_fwd f;
     setup_ray(g, &cams[cam_id[i]], pix[i], op, &r);
-    forward_ray(g, &r, r.o, r.d, op, &f);
+    forward_ray(g, &r, r.o, r.d, r.Y, op, &f);
     const double Dt = target_ray_depth(op, depth_t[i], r.dc_norm);
     double dL_dC[3], e2 = 0.0;
     for (int ch = 0; ch < 3; ++ch) {
@@ -440,7 +468,9 @@ double orc_grad_grid(const orc_grid *g, const orc_camera *cams, int64_t n_rays,
 /* Per valid ray: the 4x6 Jacobian of the residual (C - C_target, D - D_target)
  * with respect to xi, from Eq. 12-13 with dp/dr = [I, t_i I] (Eq. 14) and the
  * trilinear spatial derivatives of Appendix A; t_i, delta_i, the clip and the
- * SH direction are held fixed, as in the paper. Then
+ * SH direction are held fixed, as in the paper (with op->dir_term, the variant,
+ * the colour rows also get sum_i w_i dc_i/dchat sum_k f_k dY_k/dd through d).
+ * Then
  *   H = sum J^T W J, b = sum J^T W r, loss = sum r^T W r
  * with W = diag(1,1,1,lambda_d)/M. J [n][4][6] and r [n][4] may be NULL;
  * invalid rays get zero rows. */
@@ -462,7 +492,7 @@ double orc_pose_jacobian(const orc_grid *g, const orc_camera *cams,
     orc_ray r;
     orc_fwd f;
     setup_ray(g, &cams[cam_id[i]], pix[i], op, &r);
-    forward_ray(g, &r, r.o, r.d, op, &f);
+    forward_ray(g, &r, r.o, r.d, r.Y, op, &f);
     const double Dt = target_ray_depth(op, depth_t[i], r.dc_norm);
     double *ri = rall + 4 * i;
     for (int ch = 0; ch < 3; ++ch) ri[ch] = f.C[ch] - rgb_t[3 * i + ch];
@@ -470,6 +500,8 @@ double orc_pose_jacobian(const orc_grid *g, const orc_camera *cams,
     /* dX/do and dX/dd for X in (R, G, B, D): Eq. 12, 13 with Eq. 14 */
     double dX_do[4][3] = {{0}}, dX_dd[4][3] = {{0}};
     double tau = 0.0, S[3] = {0, 0, 0}, SD = 0.0;
+    double dY[9][3];
+    orc_sh_basis_grad(r.d, dY);
     for (int64_t k = 0; k < r.n; ++k) {
       const double t = r.t_min + (k + 0.5) * op->step;
       const double delta = op->step;
@@ -492,6 +524,13 @@ double orc_pose_jacobian(const orc_grid *g, const orc_camera *cams,
       }
       const double dD_dsig = delta * (t * T_next - f.D + SD); /* Eq. 10 */
       for (int a = 0; a < 3; ++a) dX_dp[3][a] = dD_dsig * dsig_dp[a];
+      if (op->dir_term) /* variant: c_i also depends on d through Y(d) */
+        for (int ch = 0; ch < 3; ++ch)
+          for (int a = 0; a < 3; ++a) {
+            double gy = 0.0;
+            for (int k = 0; k < 9; ++k) gy += s.f_sh[ch][k] * dY[k][a];
+            dX_dd[ch][a] += w * s.dc_dchat[ch] * gy;
+          }
       for (int x = 0; x < 4; ++x)
         for (int a = 0; a < 3; ++a) {
           dX_do[x][a] += dX_dp[x][a];      /* dp/do = I   */

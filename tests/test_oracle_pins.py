@@ -348,6 +348,47 @@ def test_pose_jacobian_matches_frozen_sample_differences():
     np.testing.assert_array_equal(f0.rgb, r0.rgb)
 
 
+def test_sh_basis_gradient_matches_differences():
+    rng = np.random.default_rng(12)
+    for _ in range(5):
+        d = rng.standard_normal(3)
+        G = oracle.sh_basis_grad(d)
+        eps = 1e-6
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = eps
+            fd = (oracle.sh_basis(d + e) - oracle.sh_basis(d - e)) / (2 * eps)
+            np.testing.assert_allclose(G[:, a], fd, atol=1e-9)
+
+
+def test_pose_jacobian_view_direction_variant_matches_differences():
+    """Variant (Sec. 5.3 omits it): the SH colour also turns with the ray
+    direction. Its Jacobian matches differences of the frozen forward whose SH
+    direction follows the pose, and differs from the paper's Jacobian only in
+    the colour rows' rotation columns."""
+    g, cam, rgb_t, depth_t, opts = pose_setup()
+    ov = dict(opts, dir_term=True)
+    pj = oracle.pose_jacobian(g, [cam], ov, rgb_t, depth_t)
+    eps = 1e-6
+    fd = np.zeros_like(pj.J)
+    for j in range(6):
+        xi = np.zeros(6)
+        xi[j] = eps
+        fp = oracle.render_frozen(g, [cam], ov, xi)
+        fm = oracle.render_frozen(g, [cam], ov, -xi)
+        fd[:, :3, j] = (fp.rgb - fm.rgb) / (2 * eps)
+        fd[:, 3, j] = (fp.depth - fm.depth) / (2 * eps)
+    valid = np.isfinite(depth_t) & (depth_t > 0)
+    fd[~valid] = 0
+    scale = np.abs(pj.J).max()
+    assert np.abs(fd - pj.J).max() <= 1e-5 * scale
+    base = oracle.pose_jacobian(g, [cam], opts, rgb_t, depth_t)
+    diff = pj.J - base.J
+    assert np.abs(diff[:, :3, 3:]).max() > 1e-3 * scale
+    assert np.abs(diff[:, :3, :3]).max() <= 1e-12 * scale
+    assert np.abs(diff[:, 3, :]).max() <= 1e-12 * scale
+
+
 def test_pose_gradient_b_is_half_loss_gradient():
     """b = sum J^T W r, so d loss / d xi = 2 b (Eq. 4, 5, 11 chained with Eq. 12-14)."""
     g, cam, rgb_t, depth_t, opts = pose_setup()
