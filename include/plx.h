@@ -117,6 +117,13 @@ typedef struct {
   const int32_t *pixel;  /* DEVICE [n_rays] or NULL */
 } plx_rays;
 
+/* plx_render_opts.pose_flags. PLX_POSE_VIEW_DIR: the pose Jacobian also
+ * differentiates the SH colour through the ray direction, dc/dd (a variant:
+ * Sec. 5.3 holds the SH direction fixed). Honoured by plx_render_backward_pose,
+ * plx_render_backward_pose_noalloc and plx_track_adam_step; the batched launch
+ * rejects it. */
+#define PLX_POSE_VIEW_DIR 1
+
 typedef struct {
   double step;         /* sample spacing delta in world units, > 0 */
   double near_t;       /* smallest t marched, >= 0 */
@@ -126,7 +133,7 @@ typedef struct {
   int32_t max_samples; /* cap on samples per ray, >= 0 */
   int32_t color_act;   /* plx_color_act */
   int32_t depth_is_z;  /* 1: depth targets are z-depths; 0: ray distances */
-  int32_t reserved;
+  int32_t pose_flags;  /* 0, or PLX_POSE_VIEW_DIR (pose calls only) */
 } plx_render_opts;
 
 const char *plx_last_error(void);

@@ -382,6 +382,8 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
   if (o->color_act != PLX_ACT_SIGMOID && o->color_act != PLX_ACT_IDENTITY)
     return fail(PLX_EINVAL, "%s: unknown color_act %d", what, o->color_act);
   if (fixed_cam >= cams->n_cams) return fail(PLX_EINVAL, "%s: cam %d out of range", what, fixed_cam);
+  if (o->pose_flags & ~PLX_POSE_VIEW_DIR)
+    return fail(PLX_EINVAL, "%s: unknown pose_flags 0x%x", what, o->pose_flags);
   std::memset(&P, 0, sizeof(P));
   P.g.links = g->links;
   P.g.rec = g->rec;
@@ -414,6 +416,7 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
   P.o.max_samples = o->max_samples;
   P.o.color_act = o->color_act;
   P.o.depth_is_z = o->depth_is_z;
+  P.o.dir_term = (o->pose_flags & PLX_POSE_VIEW_DIR) ? 1 : 0;
   P.poses = cams->poses;
   P.err = &reinterpret_cast<Workspace*>(g->ws)->err;
   P.ct.n_cams = cams->n_cams;
@@ -573,6 +576,8 @@ extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cam
   dense.cam_id = nullptr;
   dense.pixel = nullptr;
   Common P;
+  if (opts && (opts->pose_flags & PLX_POSE_VIEW_DIR))
+    return fail(PLX_EINVAL, "%s: the view-direction variant is not in the batched launch", what);
   plx_status st = build_common(what, g, cams, &dense, opts, -1, P);
   if (st != PLX_OK) return st;
   const CamTable base = P.ct;

@@ -121,6 +121,7 @@ struct Opts {
   int32_t max_samples;
   int32_t color_act;
   int32_t depth_is_z;
+  int32_t dir_term;               // pose Jacobian: add the SH view-direction term
 };
 
 struct Common {

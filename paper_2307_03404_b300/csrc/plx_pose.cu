@@ -12,6 +12,9 @@
 // forms dX/do = P_X - X Q, dX/dd = P^t_X - X Q^t once X is known. The chain to
 // the left perturbation xi = (rho, phi) of the pose is
 //   dX/drho = dX/do,  dX/dphi = o x dX/do + d x dX/dd.
+// The view-direction variant (not in the paper) adds to the colour rows'
+// dX/dd the derivative of the SH colour through Y(d), gathered per cell
+// (plx_pose_march.cuh: dir_flush).
 //
 // Reduction: per ray 29 values (21 of J^T W J, 6 of J^T W r, r^T W r, valid
 // count) are formed in FP32 from the FP32 Jacobian. A warp reduce-scatter in
@@ -23,7 +26,7 @@
 
 namespace plx {
 
-template <int STORE, int MINB>
+template <int STORE, int MINB, bool DIRT = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
                 const float* __restrict__ depth_t, double* __restrict__ partials,
@@ -44,7 +47,8 @@ k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_
     setup_ray(P, id, r, lane);
     float dz = 0.f;
     if (id.valid) dz = __ldg(depth_t + id.out);
-    if (id.valid && depth_valid(dz)) pose_ray_values<STORE>(P, r, rgb_t + 3 * id.out, dz, v);
+    if (id.valid && depth_valid(dz))
+      pose_ray_values<STORE, DIRT>(P, r, rgb_t + 3 * id.out, dz, v);
     acc += warp_reduce_scatter(v, lane);
   }
   red[warp][lane] = acc;
@@ -146,7 +150,14 @@ void launch_backward_pose(int store, int minb, const Common& P, const float* rgb
 #define PLX_POSE(S, M)                                                                 \
   k_backward_pose<S, M><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, partials, retire, \
                                                   JtWJ, JtWr, loss)
-  PLX_DISPATCH_SM(store, minb, PLX_POSE);
+#define PLX_POSE_DIR(S, M)                                                             \
+  k_backward_pose<S, M, true><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, partials,   \
+                                                        retire, JtWJ, JtWr, loss)
+  if (P.o.dir_term)
+    PLX_DISPATCH_SM(store, minb, PLX_POSE_DIR);
+  else
+    PLX_DISPATCH_SM(store, minb, PLX_POSE);
+#undef PLX_POSE_DIR
 #undef PLX_POSE
 }
 

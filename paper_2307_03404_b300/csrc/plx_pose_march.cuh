@@ -21,9 +21,46 @@ __device__ __forceinline__ void grad_local(const float V[8], float x, float y, f
 struct PoseAcc {
   float Po[4][3], Pd[4][3];  // per output X in (R, G, B, D)
   float Qo[3], Qd[3];
+  float G[3][3];             // view-direction variant: d C_ch / d d through Y(d)
 };
 
+// sum_k k9[k] grad Y_k(d): the gradient of the SH sum with respect to the
+// direction, from the polynomials of sh_basis.
+__device__ __forceinline__ void sh_dir_grad(const float d[3], const float* k9, float q[3]) {
+  const float c1 = 0.48860251190291992f, c2 = 1.09254843059207907f;
+  const float c20 = 0.31539156525252005f, c22 = 0.54627421529603959f;
+  const float x = d[0], y = d[1], z = d[2];
+  q[0] = c1 * k9[3] + c2 * (y * k9[4] + z * k9[7]) + 2.f * c22 * x * k9[8];
+  q[1] = c1 * k9[1] + c2 * (x * k9[4] + z * k9[5]) - 2.f * c22 * y * k9[8];
+  q[2] = c1 * k9[2] + c2 * (y * k9[5] + x * k9[7]) + 6.f * c20 * z * k9[6];
+}
+
+// View-direction variant: the per-corner weights sum_i w_i dc_i/dchat w_c(p_i)
+// gathered over the samples a ray took in one cell are applied when it leaves
+// the cell, to the corner's SH sum differentiated in the direction (the
+// records are re-read; they were loaded for this cell moments before).
 template <int STORE>
+__device__ __forceinline__ void dir_flush(const GridView& g, const int32_t l[8], float Ac[8][3],
+                                          const float d[3], float G[3][3]) {
+#pragma unroll 1
+  for (int c = 0; c < 8; ++c) {
+    if (l[c] >= 0 && (Ac[c][0] != 0.f || Ac[c][1] != 0.f || Ac[c][2] != 0.f)) {
+      float v[28];
+      load_record<STORE>(g.rec, l[c], v);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float q[3];
+        sh_dir_grad(d, v + 1 + 9 * ch, q);
+        G[ch][0] = fmaf(Ac[c][ch], q[0], G[ch][0]);
+        G[ch][1] = fmaf(Ac[c][ch], q[1], G[ch][1]);
+        G[ch][2] = fmaf(Ac[c][ch], q[2], G[ch][2]);
+      }
+    }
+    Ac[c][0] = Ac[c][1] = Ac[c][2] = 0.f;
+  }
+}
+
+template <int STORE, bool DIRT = false>
 __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const float Y[9],
                                            float C[3], float& D, float& T, PoseAcc& A) {
   const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
@@ -33,6 +70,11 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
   int32_t l[8];
   float cs[8], cc[8][3];
   float S[3] = {0.f, 0.f, 0.f}, SD = 0.f;
+  float Ac[DIRT ? 8 : 1][3];
+  if constexpr (DIRT) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) Ac[c][0] = Ac[c][1] = Ac[c][2] = 0.f;
+  }
   T = 1.f;
   const float dt = r.dt;
   for (int k = 0; k < r.n; ++k) {
@@ -43,6 +85,9 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
     sample_axis(r.bh[1], r.bl[1], r.sh[1], r.sl[1], kf, rm2y, iy, fy);
     sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
     if (ix != cx || iy != cy || iz != cz) {
+      if constexpr (DIRT) {
+        if (!empty) dir_flush<STORE>(P.g, l, Ac, r.dir, A.G);
+      }
       cx = ix; cy = iy; cz = iz;
       if (block_empty(P.g, ix, iy, iz)) {
         empty = true;
@@ -79,6 +124,10 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
       S[ch] = fmaf(wgt, col, S[ch]);
       const float cs_coef = dt * (col * Tn + S[ch]);
       const float cc_coef = wgt * dact;
+      if constexpr (DIRT) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) Ac[c][ch] = fmaf(cc_coef, w[c], Ac[c][ch]);
+      }
       const float u0 = cs_coef * gsig[0] + cc_coef * gch[0] * ihx;
       const float u1 = cs_coef * gsig[1] + cc_coef * gch[1] * ihy;
       const float u2 = cs_coef * gsig[2] + cc_coef * gch[2] * ihz;
@@ -100,6 +149,9 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
     }
     T = Tn;
     if (T < P.o.stop_T) break;
+  }
+  if constexpr (DIRT) {
+    if (!empty) dir_flush<STORE>(P.g, l, Ac, r.dir, A.G);
   }
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], S[ch]);
@@ -144,7 +196,7 @@ __device__ __forceinline__ double warp_reduce_scatter(const float v[32], int lan
 // triangle of J^T W J (index hidx), v[21..26] = J^T W r, v[27] = r^T W r,
 // v[28] = 1 (count), with W = diag(1, 1, 1, lambda_d) (1/M is applied after the
 // reduction). rgb_t points at the ray's colour target, dz is its depth target.
-template <int STORE>
+template <int STORE, bool DIRT = false>
 __device__ __forceinline__ void pose_ray_values(const Common& P, const RayF& r,
                                                 const float* __restrict__ rgb_t, float dz,
                                                 float v[32]) {
@@ -158,8 +210,10 @@ __device__ __forceinline__ void pose_ray_values(const Common& P, const RayF& r,
     for (int a = 0; a < 3; ++a) A.Po[x][a] = A.Pd[x][a] = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) A.Qo[a] = A.Qd[a] = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) A.G[ch][0] = A.G[ch][1] = A.G[ch][2] = 0.f;
   float C[3], D, T;
-  march_pose<STORE>(P, r, Y, C, D, T, A);
+  march_pose<STORE, DIRT>(P, r, Y, C, D, T, A);
   const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
   float res[4], J[4][6];
 #pragma unroll
@@ -171,6 +225,9 @@ __device__ __forceinline__ void pose_ray_values(const Common& P, const RayF& r,
     for (int a = 0; a < 3; ++a) {
       jo[a] = A.Po[x][a] - X * A.Qo[a];
       jd[a] = A.Pd[x][a] - X * A.Qd[a];
+      if constexpr (DIRT) {
+        if (x < 3) jd[a] += A.G[x][a];
+      }
     }
     const float* o = r.org;
     const float* d = r.dir;

@@ -25,6 +25,7 @@ STORAGE = {"f32": STORE_F32, "bf16": STORE_BF16, "f16": STORE_F16, "f32_bf16": S
 ACT_SIGMOID, ACT_IDENTITY = 0, 1
 MAX_CAMERAS = 128
 GRAD_STRIDE = 32
+POSE_VIEW_DIR = 1
 
 STATUS = {0: "PLX_OK", 1: "PLX_EINVAL", 2: "PLX_ENOMEM", 3: "PLX_ECUDA",
           4: "PLX_EDEVICE_CHECK", 5: "PLX_ETIMEOUT", 6: "PLX_EUNSUPPORTED"}
@@ -71,7 +72,7 @@ class LaunchConfig(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("step", C.c_double), ("near_t", C.c_double), ("stop_T", C.c_double),
                 ("bg", C.c_float * 3), ("lambda_d", C.c_float), ("max_samples", C.c_int32),
-                ("color_act", C.c_int32), ("depth_is_z", C.c_int32), ("reserved", C.c_int32)]
+                ("color_act", C.c_int32), ("depth_is_z", C.c_int32), ("pose_flags", C.c_int32)]
 
 
 SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload",
@@ -276,7 +277,7 @@ def make_rays(cam_id=None, pixel=None):
 
 
 def make_opts(step, near=0.0, stop_T=0.0, bg=(0.0, 0.0, 0.0), lambda_d=1.0,
-              max_samples=1 << 30, color_act="sigmoid", depth_is_z=True):
+              max_samples=1 << 30, color_act="sigmoid", depth_is_z=True, view_dir=False):
     o = RenderOpts()
     o.step, o.near_t, o.stop_T = float(step), float(near), float(stop_T)
     o.bg[:] = [float(v) for v in bg]
@@ -284,13 +285,15 @@ def make_opts(step, near=0.0, stop_T=0.0, bg=(0.0, 0.0, 0.0), lambda_d=1.0,
     o.max_samples = int(min(max_samples, 2 ** 31 - 1))
     o.color_act = {"sigmoid": ACT_SIGMOID, "identity": ACT_IDENTITY}[color_act]
     o.depth_is_z = int(bool(depth_is_z))
+    o.pose_flags = POSE_VIEW_DIR if view_dir else 0
     return o
 
 
 def opts_from_dict(d):
     return make_opts(d["step"], d.get("near", 0.0), d.get("stop_T", 0.0), d.get("bg", (0, 0, 0)),
                      d.get("lambda_d", 1.0), d.get("max_samples", 1 << 30),
-                     d.get("color_act", "sigmoid"), d.get("depth_is_z", True))
+                     d.get("color_act", "sigmoid"), d.get("depth_is_z", True),
+                     d.get("dir_term", False))
 
 
 # ----------------------------------------------------------- entry points

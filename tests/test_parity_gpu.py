@@ -213,6 +213,46 @@ def test_backward_pose_matches_oracle(sphere):
     np.testing.assert_array_equal(b2, b3)
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_backward_pose_view_direction_variant(sphere, storage):
+    """PLX_POSE_VIEW_DIR (the SH colour also turns with the ray): the pose
+    system against the oracle's variant, on dense and list rays; it differs
+    from the paper's system, and the batched launch rejects the flag. Colour
+    only (lambda_d = 0), identity activation and 4x SH, so the term is large
+    enough to tell the two systems apart at the tolerance."""
+    g0, cam, _, opts = sphere
+    g = g0.with_values(g0.density, 4.0 * g0.sh)
+    opts = dict(opts, depth_is_z=False, lambda_d=0.0, bg=(0.1, 0.1, 0.2), color_act="identity")
+    ref_t = oracle.render(g, [cam], opts)
+    T0 = scenes.perturb_pose(cam.T_wc, 0.03, 2.0, np.random.default_rng(9))
+    cam0 = cam.with_pose(T0)
+    rgb_t = ref_t.rgb.astype(np.float32)
+    depth_t = ref_t.depth.astype(np.float32)
+    gr = g
+    if storage == "bf16":
+        gr = g.with_values(torch.from_numpy(g.density).bfloat16().float().numpy(),
+                           torch.from_numpy(g.sh).bfloat16().float().numpy())
+    case = GpuCase(g, [cam0], storage=storage)
+    ov = dict(opts, dir_term=True)
+    H, b, loss = case.backward_pose(ov, 0, rgb_t, depth_t)
+    ref = oracle.pose_jacobian(gr, [cam0], ov, rgb_t, depth_t)
+    base = oracle.pose_jacobian(gr, [cam0], opts, rgb_t, depth_t)
+    assert loss[1] == ref.M
+    assert abs(loss[0] - ref.loss) <= 1e-5 * ref.loss
+    assert norm_err(H, ref.H) <= TOL_GRAD
+    assert norm_err(b, ref.b) <= TOL_GRAD
+    assert norm_err(base.b, ref.b) > 10 * TOL_GRAD       # the term matters here
+    pix = np.random.default_rng(2).permutation(cam.width * cam.height)[:700].astype(np.int32)
+    H2, b2, _ = case.backward_pose(ov, 0, rgb_t[pix], depth_t[pix], pixels=pix)
+    ref2 = oracle.pose_jacobian(gr, [cam0], ov, rgb_t[pix], depth_t[pix],
+                                rays=(np.zeros(700, np.int32), pix))
+    assert norm_err(H2, ref2.H) <= TOL_GRAD
+    assert norm_err(b2, ref2.b) <= TOL_GRAD
+    with pytest.raises(plx.PlxError, match="view-direction"):
+        plx.render_batch(case.grid, case.cams, [(0, plx.WORK_TRACK)], plx.opts_from_dict(ov),
+                         dev(rgb_t), dev(depth_t))
+
+
 def test_pose_step_matches_oracle():
     rng = np.random.default_rng(12)
     A = rng.standard_normal((9, 6))
