@@ -96,6 +96,8 @@ def _load():
     lib.orc_grow.argtypes = [P, P, P, P, C.c_int64, P, C.c_int32, P, C.c_int32, C.c_double]
     lib.orc_pose_step.restype = C.c_int
     lib.orc_grow.restype = C.c_int64
+    lib.orc_pose_step_lm.argtypes = [P, P, C.c_double, P, C.c_double, C.c_double, P, P]
+    lib.orc_pose_step_lm.restype = C.c_int
     _lib = lib
     return lib
 
@@ -289,6 +291,20 @@ def pose_step(H, b, T_wc, damping=0.0):
     xi = np.zeros(6)
     st = _load().orc_pose_step(_ptr(H), _ptr(b), C.c_double(damping), _ptr(T), _ptr(xi))
     return T.reshape(3, 4), xi, st == 0
+
+
+def pose_step_lm(H, b, loss, state, T_wc, lambda_init=1e-3, factor=10.0):
+    """Levenberg-Marquardt pose step (see orc_pose_step_lm): returns (new pose
+    [3, 4], xi, status); ``state`` (float64 [64], zeroed before the first
+    call) is updated in place."""
+    H = _f64(H, (36,))
+    b = _f64(b, (6,))
+    T = _f64(T_wc, (12,)).copy()
+    assert state.dtype == np.float64 and state.shape == (64,) and state.flags.c_contiguous
+    xi = np.zeros(6)
+    st = _load().orc_pose_step_lm(_ptr(H), _ptr(b), C.c_double(float(loss)), _ptr(state),
+                                  C.c_double(lambda_init), C.c_double(factor), _ptr(T), _ptr(xi))
+    return T.reshape(3, 4), xi, int(st)
 
 
 def sh_basis(d):

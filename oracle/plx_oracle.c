@@ -724,3 +724,87 @@ int64_t orc_grow(const int32_t res[3], const double lo[3], const double hi[3],
   free(mark);
   return added;
 }
+
+/* ---------------------------------------------- Levenberg-Marquardt step */
+/* Gauss-Newton with Marquardt's damping (the paper optimises the pose with
+ * Adam, Sec. 5.4; the plain GN step of Sec. 5.3 can overshoot where the
+ * density ramps are steep). One call per Jacobian evaluation at the current
+ * pose, with that pose's loss. state[64]: [0] lambda, [1] loss of the last
+ * accepted pose, [2] calls made, [3] 1 if this call accepted, [4..15] the
+ * accepted pose, [16..51] its H, [52..57] its b; zero it before the first
+ * call. A call accepts the current pose when it is the first or its loss is
+ * not above the last accepted one (then lambda /= factor, at least 1e-12),
+ * else restores the accepted pose (lambda *= factor, at most 1e12). It then
+ * solves (H + lambda (diag H + 1e-12 max diag H)) xi = -b with the accepted
+ * pose's H, b (lambda grows by factor while that is not positive definite,
+ * up to 8 times) and sets pose <- exp(xi^) pose. Returns 0 on an accepted
+ * pose, 2 after a rejection, 1 if no damping made the system definite (pose
+ * left at the accepted one). */
+static int solve_damped(const double H[36], const double b[6], double lam, double xi[6]) {
+  double L[6][6] = {{0}}, y[6], dmax = 0.0;
+  for (int i = 0; i < 6; ++i) dmax = H[7 * i] > dmax ? H[7 * i] : dmax;
+  for (int i = 0; i < 6; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = H[6 * i + j] + (i == j ? lam * (H[7 * i] + 1e-12 * dmax) : 0.0);
+      for (int l = 0; l < j; ++l) s -= L[i][l] * L[j][l];
+      if (i == j) {
+        if (!(s > 0.0)) return 1;
+        L[i][i] = sqrt(s);
+      } else {
+        L[i][j] = s / L[j][j];
+      }
+    }
+  }
+  for (int i = 0; i < 6; ++i) {
+    double s = -b[i];
+    for (int l = 0; l < i; ++l) s -= L[i][l] * y[l];
+    y[i] = s / L[i][i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double s = y[i];
+    for (int l = i + 1; l < 6; ++l) s -= L[l][i] * xi[l];
+    xi[i] = s / L[i][i];
+  }
+  return 0;
+}
+
+int orc_pose_step_lm(const double H[36], const double b[6], double loss, double state[64],
+                     double lambda_init, double factor, double T_wc[12], double xi_out[6]) {
+  const int first = state[2] == 0.0;
+  const int accept = first || !(loss > state[1]);
+  double lam = first ? lambda_init : state[0];
+  if (accept) {
+    if (!first) lam = lam / factor < 1e-12 ? 1e-12 : lam / factor;
+    memcpy(state + 4, T_wc, 12 * sizeof(double));
+    state[1] = loss;
+    memcpy(state + 16, H, 36 * sizeof(double));
+    memcpy(state + 52, b, 6 * sizeof(double));
+  } else {
+    lam = lam * factor > 1e12 ? 1e12 : lam * factor;
+    memcpy(T_wc, state + 4, 12 * sizeof(double));
+  }
+  double xi[6] = {0, 0, 0, 0, 0, 0};
+  int ok = 0;
+  for (int tries = 0; tries <= 8; ++tries) {
+    if (solve_damped(state + 16, state + 52, lam, xi) == 0) {
+      ok = 1;
+      break;
+    }
+    lam *= factor;
+  }
+  state[0] = lam;
+  state[2] += 1.0;
+  state[3] = accept;
+  if (xi_out) memcpy(xi_out, ok ? xi : (double[6]){0, 0, 0, 0, 0, 0}, 6 * sizeof(double));
+  if (!ok) return 1;
+  double E[12], Tn[12];
+  orc_se3_exp(xi, E);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = j == 3 ? E[4 * i + 3] : 0.0;
+      for (int l = 0; l < 3; ++l) s += E[4 * i + l] * T_wc[4 * l + j];
+      Tn[4 * i + j] = s;
+    }
+  memcpy(T_wc, Tn, sizeof(Tn));
+  return accept ? 0 : 2;
+}
