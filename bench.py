@@ -261,38 +261,68 @@ def run_ours(args):
                "loss": loss.cpu().tolist(), "launch_config": grid.get_config(),
                "tuning_trials": tuned["trials"] if tuned else None}
         if with_e2e:
+            # End to end through the public API with host buffers: each step
+            # copies its targets and poses from pinned host memory and reads
+            # its loss back. Double-buffered: the copies of step i+1 run on a
+            # copy stream while step i computes; the timed region spans all K
+            # steps, from the first copy to the last loss read.
             rgb_h = torch.from_numpy(rgb_np).pin_memory()
             depth_h = torch.from_numpy(depth_np).pin_memory()
             poses_h = cams.poses.cpu().pin_memory()
             loss_h = torch.empty(2, dtype=torch.float64).pin_memory()
-            rgb_d, depth_d = torch.empty_like(rgb_t), torch.empty_like(depth_t)
+            rgb_d = [torch.empty_like(rgb_t) for _ in range(2)]
+            depth_d = [torch.empty_like(depth_t) for _ in range(2)]
+            cams_d = [plx.CameraSet(cams_np) for _ in range(2)]
+            comp_s = torch.cuda.current_stream()
+            copy_s = torch.cuda.Stream()
+            ready = [torch.cuda.Event() for _ in range(2)]
+            free = [torch.cuda.Event() for _ in range(2)]
 
-            def e2e_step():
-                rgb_d.copy_(rgb_h, non_blocking=True)
-                depth_d.copy_(depth_h, non_blocking=True)
-                cams.poses.copy_(poses_h, non_blocking=True)
+            def prefetch(i):
+                b = i % 2
+                with torch.cuda.stream(copy_s):
+                    copy_s.wait_event(free[b])
+                    rgb_d[b].copy_(rgb_h, non_blocking=True)
+                    depth_d[b].copy_(depth_h, non_blocking=True)
+                    cams_d[b].poses.copy_(poses_h, non_blocking=True)
+                    ready[b].record(copy_s)
+
+            def compute(i):
+                b = i % 2
+                comp_s.wait_event(ready[b])
+                flush.fill_(1)
                 grad.zero_()
-                plx.render_forward(grid, cams, o, out=fw)
-                plx.render_backward_grid(grid, cams, o, rgb_d, depth_d, fw["rgb"], fw["depth"],
-                                         grad=grad, loss=loss)
+                plx.render_forward(grid, cams_d[b], o, out=fw)
+                plx.render_backward_grid(grid, cams_d[b], o, rgb_d[b], depth_d[b], fw["rgb"],
+                                         fw["depth"], grad=grad, loss=loss)
+                free[b].record(comp_s)
                 loss_h.copy_(loss, non_blocking=True)
 
-            for _ in range(W):
-                e2e_step()
+            def run(n):
+                for b in range(2):
+                    free[b].record(comp_s)
+                copy_s.wait_stream(comp_s)
+                prefetch(0)
+                for i in range(n):
+                    if i + 1 < n:
+                        prefetch(i + 1)
+                    compute(i)
+
+            run(W)
             barrier()
-            E2 = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
-            for e in E2:
-                flush.fill_(1)
-                e[0].record()
-                e2e_step()
-                e[1].record()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(comp_s)
+            run(K)
+            t1.record(comp_s)
             barrier()
-            res["e2e_ms"] = [e[0].elapsed_time(e[1]) for e in E2]
+            res["e2e_ms"] = [t0.elapsed_time(t1) / K] * K
             res["h2d"] = rgb_h.numel() * 4 + depth_h.numel() * 4 + poses_h.numel() * 8
             res["d2h"] = loss_h.numel() * 8
-        # exact sample counts for the byte model (untimed)
+        # exact sample counts for the byte model, and the vertices the step
+        # touched for the compulsory-traffic bound (untimed)
         cnt = plx.render_forward(grid, cams, o, counts=True)["counts"].cpu().numpy()
         res["counts"] = cnt
+        res["touched"] = int((grad[:, :28] != 0).any(1).sum())
         grid.close()
         return res
 
@@ -327,6 +357,10 @@ def run_ours(args):
     step_roof = (fwd_b + bwd_b) / (hbm * 1e9) * 1e3   # ms per step at the HBM roof
     fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage, valid)
 
+    # compulsory traffic of the adjoint: every touched vertex's record read
+    # once, its FP32 gradient row read and written once, its link once
+    rec_b = 128 if args.storage == "f32" else 64
+    compulsory = main["touched"] * (rec_b + 2 * 112 + 4)
     traffic = measured_traffic(dom, "room256", args.storage)
     if traffic:
         dram_gbs = traffic / (dom_ms / 1e3) / 1e9
@@ -349,9 +383,15 @@ def run_ours(args):
                      "step_frac": step_roof / (t_main / K),
                      "dram_gbs": dram_gbs if traffic else None,
                      "dram_frac": dram_gbs / hbm if traffic else None,
-                     "S_all_mean": s_all, "S_occ_mean": s_occ},
+                     "S_all_mean": s_all, "S_occ_mean": s_occ,
+                     "touched_vertices": main["touched"],
+                     "compulsory_bytes_per_launch": compulsory,
+                     "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9},
         "e2e": {"value": rays_job / (t_e2e / 1e3), "unit": "rays/s",
-                "h2d_bytes_per_step": main["h2d"], "d2h_bytes_per_step": main["d2h"]},
+                "h2d_bytes_per_step": main["h2d"], "d2h_bytes_per_step": main["d2h"],
+                "timing": "K steps as one region (first copy to last loss read); copies of "
+                          "step i+1 overlap step i on a second stream; L2 flushed per step "
+                          "inside the region"},
         "gpu_launches": K * 3,
         "clocks": clocks,
         other_storage: {"value": rays_job / (t_other / 1e3), "unit": "rays/s",
@@ -374,11 +414,13 @@ def run_ours(args):
         from paper_2307_03404_b300 import pipeline
 
         t = time.time()
-        pl = pipeline.run(sc, log=log)
+        pl = pipeline.run(sc, log=log,
+                          extra_track_cfgs=[pipeline.TrackConfig(method="lm", lm_iters=10)])
         pl["wall_seconds"] = time.time() - t
         pl["workload"] = ("room256 geometry, 300-frame 640x480 sequence (path_m long), every 10th "
                           "frame mapped into a dynamic 256^3 grid grown from depth, every frame "
-                          "tracked (Adam, 200 iterations of 4096 random rays, one CUDA graph)")
+                          "tracked (Adam, 200 iterations of 4096 random rays, one CUDA graph; again with "
+                          "10 Levenberg-Marquardt iterations on whole frames)")
         line["pipeline"] = pl
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(sc, cams_np, rgb_np, depth_np, opts, args.cpu_seconds)
@@ -404,10 +446,10 @@ def run_tracking(args, world, rank, barrier):
     T0 = scenes.perturb_pose(cam.T_wc, 0.03, 2.0, np.random.default_rng(seed + 5))
     iters = args.tracking_iters
     out = {"workload": f"{args.tracking_workload}: {R}^3 grid, {sc.grid.n_alloc} allocated, "
-                       f"one 640x480 frame, {iters} GN iterations per CUDA graph, "
+                       f"one 640x480 frame, {iters} Gauss-Newton iterations per CUDA graph, "
                        "targets rendered at the true pose, start perturbed 3 cm / 2 deg",
            "unit": "iters/s"}
-    for storage in ("f32", "bf16"):
+    for storage, method in (("f32", "lm"), ("bf16", "lm"), ("f32", "gn")):
         grid = plx.Grid.from_scene(sc.grid, storage)
         cams = plx.CameraSet([cam])
         tg = plx.render_forward(grid, cams, o)       # targets at the true pose
@@ -423,24 +465,33 @@ def run_tracking(args, world, rank, barrier):
         H = torch.empty(6, 6, device="cuda", dtype=torch.float64)
         b = torch.empty(6, device="cuda", dtype=torch.float64)
         loss = torch.empty(2, device="cuda", dtype=torch.float64)
+        lm = plx.lm_state()
         pose = cams.poses[0]
-        plx.render_backward_pose(grid, cams, 0, o, rgb_t, depth_t, out=(H, b, loss))
-        plx.pose_step(H, b, pose)
+
+        def one_iteration():
+            plx.render_backward_pose(grid, cams, 0, o, rgb_t, depth_t, out=(H, b, loss))
+            if method == "lm":
+                plx.pose_step_lm(H, b, loss, lm, pose)
+            else:
+                plx.pose_step(H, b, pose)
+
+        one_iteration()
         torch.cuda.synchronize()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=s):
             for _ in range(iters):
-                plx.render_backward_pose(grid, cams, 0, o, rgb_t, depth_t, out=(H, b, loss))
-                plx.pose_step(H, b, pose)
+                one_iteration()
         for _ in range(args.warmup):
             cams.poses.copy_(start)
+            lm.zero_()
             g.replay()
         barrier()
         evs = []
         for _ in range(max(1, args.steps // 2)):
             cams.poses.copy_(start)
+            lm.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             g.replay()
@@ -448,12 +499,19 @@ def run_tracking(args, world, rank, barrier):
             evs.append((e0, e1))
         barrier()
         ms = [a.elapsed_time(b_) for a, b_ in evs]
-        err = float(np.abs(pose.cpu().numpy().reshape(3, 4) - cam.T_wc).max())
-        out[storage] = {"value": iters * len(ms) / (sum(ms) / 1e3),
-                        "ms_per_iter": sum(ms) / len(ms) / iters,
-                        "launch_config": grid.get_config(),
-                        "start_pose_err": float(np.abs(T0 - cam.T_wc).max()),
-                        "final_pose_err": err, "final_loss": float(loss[0].item())}
+        T = pose.cpu().numpy().reshape(3, 4)
+        res = {"value": iters * len(ms) / (sum(ms) / 1e3),
+               "ms_per_iter": sum(ms) / len(ms) / iters,
+               "step": ("Gauss-Newton with Marquardt damping, accept/reject on the loss "
+                        "(plx_pose_step_lm)" if method == "lm" else
+                        "undamped Gauss-Newton (plx_pose_step)"),
+               "launch_config": grid.get_config(),
+               "start_err_cm_deg": [float(100 * np.abs(T0[:, 3] - cam.T_wc[:, 3]).max()),
+                                    float(np.degrees(np.abs(T0[:, :3] - cam.T_wc[:, :3]).max()))],
+               "final_err_cm_deg": [float(100 * np.abs(T[:, 3] - cam.T_wc[:, 3]).max()),
+                                    float(np.degrees(np.abs(T[:, :3] - cam.T_wc[:, :3]).max()))],
+               "final_loss": float(loss[0].item())}
+        out[storage if method == "lm" else "gn_undamped_f32"] = res
         grid.close()
     # the paper's tracker (Sec. 5.4): Adam on random rays of the frame
     n_rays, lr, aiters = args.adam_rays, args.adam_lr, args.adam_iters
@@ -661,6 +719,8 @@ def run_large_bench(args, barrier):
     fwd_b, bwd_b, s_all, s_occ = bytes_model(counts, storage, valid)
     hbm, peak_kind = peaks()
     achieved = bwd_b / (bwd_ms / 1e3) / 1e9
+    touched = int((grad[:, :28] != 0).any(1).sum())
+    compulsory = touched * (64 + 2 * 112 + 4)
     out = {"workload": f"house1024: 1024^3 grid, {n_alloc} allocated "
                        f"({n_alloc / 1024 ** 3:.2%}), {storage} storage, 16 x 1200x680 keyframes "
                        f"({n_rays} rays), step 0.5 voxel, <= 2048 samples per ray",
@@ -670,7 +730,10 @@ def run_large_bench(args, barrier):
                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_launch": bwd_b,
                         "step_frac": (fwd_b + bwd_b) / (hbm * 1e9) * 1e3 / step_ms,
-                        "S_all_mean": s_all, "S_occ_mean": s_occ},
+                        "S_all_mean": s_all, "S_occ_mean": s_occ,
+                        "touched_vertices": touched,
+                        "compulsory_bytes_per_launch": compulsory,
+                        "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9},
            "loss": loss.cpu().tolist(), "launch_config": grid.get_config(),
            "autotuned": tuned is not None, "steps": K}
     grid.close()
@@ -698,9 +761,19 @@ def cpu_baseline(sc, cams, rgb_np, depth_np, opts, seconds):
         done += 2048
         i += 1
     dt = time.time() - t0
+    # one thread, one chunk of 1024 rays
+    oracle.set_threads(1)
+    cid, pix = scenes.random_rays(cams, 1024, 999)
+    rows = offs[cid] + pix
+    t1 = time.time()
+    oracle.grad_grid(sc.grid, cams, opts, rgb_np[rows], depth_np[rows], rays=(cid, pix))
+    dt1 = time.time() - t1
+    oracle.set_threads(cores)
     return {"value": done / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} seeded random rays of the same 8 keyframes in chunks of 2048 "
-                      f"(forward + loss + grid gradient, FP64, OpenMP over rays), {dt:.1f} s"}
+                      f"(forward + loss + grid gradient, FP64, OpenMP over rays), {dt:.1f} s",
+            "single_thread": {"value": 1024 / dt1, "unit": "rays/s", "cores": 1,
+                              "sample": f"1024 seeded random rays, {dt1:.1f} s"}}
 
 
 def run_reference(args):

@@ -271,6 +271,34 @@ plx_status plx_pose_step(const double *JtWJ, const double *JtWr, double damping,
                          double *pose, double *xi_out, int32_t *status,
                          void *stream);
 
+/* Sec. 5.3 with Marquardt's damping (the paper optimises the pose with Adam,
+ * Sec. 5.4; a plain Gauss-Newton step can overshoot where the density ramps
+ * are steep). One call per Jacobian evaluation at the current pose, passing
+ * that pose's system and loss:
+ *   - the current pose is accepted if this is the first call (state[2] == 0)
+ *     or its loss is not above the last accepted one; lambda /= factor (not
+ *     below 1e-12, and lambda = lambda_init on the first call);
+ *   - otherwise the last accepted pose is restored, lambda *= factor (not
+ *     above 1e12), and its system is used instead;
+ *   - then (H + lambda (diag H + 1e-12 max diag H)) xi = -b is solved by
+ *     Cholesky in FP64 (lambda grows by factor up to 8 times while that is not
+ *     positive definite) and pose <- exp(xi^) pose.
+ *   JtWJ, JtWr, loss  DEVICE, as written by plx_render_backward_pose
+ *   state   DEVICE double [64], zeroed by the caller before the first call:
+ *           [0] lambda, [1] loss of the accepted pose, [2] calls made, [3] 1
+ *           if this call accepted, [4..15] accepted pose, [16..51] its H,
+ *           [52..57] its b
+ *   pose    DEVICE double [12], updated in place
+ *   xi_out  DEVICE double [6] or NULL; status DEVICE int32 [1] or NULL: 0
+ *           accepted, 2 rejected and restored, 1 no damping made the system
+ *           definite (pose left at the accepted one)
+ * Asynchronous; graph-capturable. Errors: PLX_EINVAL (lambda_init < 0,
+ * factor <= 1, null pointers). */
+plx_status plx_pose_step_lm(const double *JtWJ, const double *JtWr,
+                            const double *loss, double *state,
+                            double lambda_init, double factor, double *pose,
+                            double *xi_out, int32_t *status, void *stream);
+
 /* Sec. 5.4 (RMSProp for the mapping). One RMSProp step on every stored grid
  * value, in place, from the gradient left by plx_render_backward_grid:
  *   v <- alpha v + (1 - alpha) g^2,  value <- value - lr g / (sqrt(v) + eps)

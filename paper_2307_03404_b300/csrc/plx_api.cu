@@ -27,6 +27,9 @@ int batch_kernel_blocks_per_sm(int store, int minb);
 void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, float lr_density,
                     float lr_sh, float alpha, float eps, int zero_grad, int num_sms,
                     cudaStream_t s);
+void launch_pose_step_lm(const double* H, const double* b, const double* loss, double* state,
+                         double lambda_init, double factor, double* pose, double* xi_out,
+                         int32_t* status, cudaStream_t s);
 void launch_adam_pose(const double* JtWr, double* state, double* pose, double lr, double b1,
                       double b2, double eps, cudaStream_t s);
 void launch_batch(int store, int minb, const Common& P, int n_track, const float* rgb_t,
@@ -535,6 +538,20 @@ plx_status plx_pose_step(const double* JtWJ, const double* JtWr, double damping,
 }  // extern "C"
 
 // ------------------------------------------------------------ launch config
+extern "C" plx_status plx_pose_step_lm(const double* JtWJ, const double* JtWr, const double* loss,
+                                       double* state, double lambda_init, double factor,
+                                       double* pose, double* xi_out, int32_t* status,
+                                       void* stream) {
+  if (!JtWJ || !JtWr || !loss || !state || !pose)
+    return fail(PLX_EINVAL, "pose_step_lm: null argument");
+  if (!(lambda_init >= 0.0) || !std::isfinite(lambda_init) || !(factor > 1.0) ||
+      !std::isfinite(factor))
+    return fail(PLX_EINVAL, "pose_step_lm: need lambda_init >= 0 and factor > 1");
+  launch_pose_step_lm(JtWJ, JtWr, loss, state, lambda_init, factor, pose, xi_out, status,
+                      (cudaStream_t)stream);
+  return launch_check("pose_step_lm");
+}
+
 extern "C" plx_status plx_grid_get_config(const plx_grid* g, plx_launch_config* out) {
   if (!g || !out) return fail(PLX_EINVAL, "grid_get_config: null argument");
   *out = g->cfg;

@@ -140,6 +140,77 @@ __global__ void k_pose_step(const double* __restrict__ H, const double* __restri
   if (status) *status = 0;
 }
 
+// ---------------------------------------------------- Levenberg-Marquardt
+// Solves (H + lam (diag H + 1e-12 max diag H)) xi = -b by Cholesky; false if
+// that matrix is not positive definite.
+__device__ bool solve_marquardt(const double* H, const double* b, double lam, double xi[6]) {
+  double L[6][6], y[6], dmax = 0.0;
+  for (int i = 0; i < 6; ++i) dmax = fmax(dmax, H[7 * i]);
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) L[i][j] = 0.0;
+  for (int i = 0; i < 6; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = H[6 * i + j] + (i == j ? lam * (H[7 * i] + 1e-12 * dmax) : 0.0);
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        L[i][i] = sqrt(s);
+      } else {
+        L[i][j] = s / L[j][j];
+      }
+    }
+  }
+  for (int i = 0; i < 6; ++i) {
+    double s = -b[i];
+    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+    y[i] = s / L[i][i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < 6; ++k) s -= L[k][i] * xi[k];
+    xi[i] = s / L[i][i];
+  }
+  return true;
+}
+
+// One damped step per Jacobian evaluation; state layout in plx.h.
+__global__ void k_pose_step_lm(const double* __restrict__ H, const double* __restrict__ b,
+                               const double* __restrict__ loss, double* __restrict__ st,
+                               double lambda_init, double factor, double* __restrict__ pose,
+                               double* __restrict__ xi_out, int32_t* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const bool first = st[2] == 0.0;
+  const double L = loss[0];
+  const bool accept = first || !(L > st[1]);
+  double lam = first ? lambda_init : st[0];
+  if (accept) {
+    if (!first) lam = fmax(lam / factor, 1e-12);
+    for (int i = 0; i < 12; ++i) st[4 + i] = pose[i];
+    st[1] = L;
+    for (int i = 0; i < 36; ++i) st[16 + i] = H[i];
+    for (int i = 0; i < 6; ++i) st[52 + i] = b[i];
+  } else {
+    lam = fmin(lam * factor, 1e12);
+    for (int i = 0; i < 12; ++i) pose[i] = st[4 + i];
+  }
+  double xi[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  bool ok = false;
+  for (int tries = 0; tries <= 8 && !ok; ++tries) {
+    ok = solve_marquardt(st + 16, st + 52, lam, xi);
+    if (!ok) lam *= factor;
+  }
+  st[0] = lam;
+  st[2] += 1.0;
+  st[3] = accept ? 1.0 : 0.0;
+  if (!ok)
+    for (int q = 0; q < 6; ++q) xi[q] = 0.0;
+  else
+    se3_exp_left(xi, pose);
+  if (xi_out)
+    for (int q = 0; q < 6; ++q) xi_out[q] = xi[q];
+  if (status) *status = !ok ? 1 : (accept ? 0 : 2);
+}
+
 // ------------------------------------------------------------ host launch
 void launch_backward_pose(int store, int minb, const Common& P, const float* rgb_t,
                           const float* depth_t, double* partials, unsigned* retire, double* JtWJ,
@@ -164,6 +235,12 @@ void launch_backward_pose(int store, int minb, const Common& P, const float* rgb
 void launch_pose_step(const double* H, const double* b, double damping, double* pose,
                       double* xi_out, int32_t* status, cudaStream_t s) {
   k_pose_step<<<1, 32, 0, s>>>(H, b, damping, pose, xi_out, status);
+}
+
+void launch_pose_step_lm(const double* H, const double* b, const double* loss, double* state,
+                         double lambda_init, double factor, double* pose, double* xi_out,
+                         int32_t* status, cudaStream_t s) {
+  k_pose_step_lm<<<1, 32, 0, s>>>(H, b, loss, state, lambda_init, factor, pose, xi_out, status);
 }
 
 int pose_kernel_blocks_per_sm(int store, int minb) {

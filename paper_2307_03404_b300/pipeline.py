@@ -94,6 +94,9 @@ class TrackConfig:
     eps: float = 1e-8
     constant_velocity: bool = True
     seed: int = 11
+    method: str = "adam"        # "adam": the paper's tracker; "lm": damped Gauss-Newton
+    lm_iters: int = 20          # LM iterations per frame (whole-frame Jacobian each)
+    lm_lambda: float = 1e-3
 
 
 def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: torch.Tensor,
@@ -184,7 +187,15 @@ def track_sequence(grid: plx.Grid, cam_list, rgb_frames, depth_frames, opts, cfg
             torch.empty(6, device="cuda", dtype=torch.float64),
             torch.empty(2, device="cuda", dtype=torch.float64))
 
+    if cfg.method == "lm":
+        state = plx.lm_state()
+
     def iterations():
+        if cfg.method == "lm":
+            for _ in range(cfg.lm_iters):
+                plx.render_backward_pose(grid, one, 0, opts, rgb_buf, depth_buf, out=outs)
+                plx.pose_step_lm(outs[0], outs[1], outs[2], state, one.poses[0], cfg.lm_lambda)
+            return
         for k in range(cfg.iters):
             lr = cfg.lr * (cfg.lr_final / cfg.lr) ** (k / max(1, cfg.iters - 1))
             plx.track_adam_step(grid, one, 0, opts, cfg.n_rays, cfg.seed, rgb_buf, depth_buf, state,
@@ -195,8 +206,11 @@ def track_sequence(grid: plx.Grid, cam_list, rgb_frames, depth_frames, opts, cfg
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         state.zero_()
-        plx.track_adam_step(grid, one, 0, opts, cfg.n_rays, cfg.seed, rgb_buf, depth_buf, state,
-                            cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, out=outs)
+        if cfg.method == "lm":
+            plx.render_backward_pose(grid, one, 0, opts, rgb_buf, depth_buf, out=outs)
+        else:
+            plx.track_adam_step(grid, one, 0, opts, cfg.n_rays, cfg.seed, rgb_buf, depth_buf,
+                                state, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, out=outs)
     torch.cuda.current_stream().wait_stream(s)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
@@ -233,13 +247,14 @@ def track_sequence(grid: plx.Grid, cam_list, rgb_frames, depth_frames, opts, cfg
 
 
 def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", depth_noise=0.0025,
-        map_cfg=None, track_cfg=None, seed=21, log=None):
+        map_cfg=None, track_cfg=None, extra_track_cfgs=(), seed=21, log=None):
     """Whole pipeline on a synthetic room: a smooth sequence of ``n_frames``
     640x480 RGB-D frames along the first ``span`` of a spline path (depth
     noise N(0, (depth_noise z^2)^2), 2% of depths missing), every
     ``map_every``-th frame mapped with its true pose into a ``res``^3 dynamic
-    grid over the scene's box, every frame tracked from the first true pose.
-    Returns a dict of metrics and timings."""
+    grid over the scene's box, every frame tracked from the first true pose
+    with ``track_cfg`` (and again with each of ``extra_track_cfgs``, on the
+    same map). Returns a dict of metrics and timings."""
     from . import scenes
 
     map_cfg = map_cfg or MapConfig()
@@ -266,17 +281,24 @@ def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", de
     t_map = time.time() - t0
     mm = mapping_metrics(dg.grid, cams_np, rgb, depth, opts)
     gt = np.array([np.asarray(c.T_wc, np.float64).reshape(3, 4) for c in cams_np])
-    est, ms_frame = track_sequence(dg.grid, cams_np, rgb, depth, opts, track_cfg, log=log)
-    t_rpe, r_rpe = trajectory.rpe(est, gt)
-    err = np.linalg.norm(est[:, :, 3] - gt[:, :, 3], axis=1)
+
+    def tracked(cfg):
+        est, ms_frame = track_sequence(dg.grid, cams_np, rgb, depth, opts, cfg, log=log)
+        t_rpe, r_rpe = trajectory.rpe(est, gt)
+        err = np.linalg.norm(est[:, :, 3] - gt[:, :, 3], axis=1)
+        desc = (f"Adam, {cfg.iters} iterations of {cfg.n_rays} random rays" if cfg.method == "adam"
+                else f"Levenberg-Marquardt, {cfg.lm_iters} whole-frame Jacobians")
+        return {"tracker": desc, "track_ms_per_frame": ms_frame,
+                "ate_m": trajectory.ate(est, gt), "rpe_t_m": t_rpe, "rpe_r_deg": r_rpe,
+                "median_err_m": float(np.median(err)), "max_err_m": float(err.max())}
+
     out = {"frames": n_frames, "keyframes": len(keys), "grid": f"{R}^3 dynamic, {storage}",
            "allocated": dg.n, "map_seconds": t_map, "map_steps": map_cfg.iters,
            "map_rays_per_step": map_cfg.rays_per_step,
            "map_loss_first_last": [float(losses[0]), float(losses[-1])],
-           "mapping": mm, "track_ms_per_frame": ms_frame, "track_iters": track_cfg.iters,
-           "track_rays": track_cfg.n_rays,
-           "ate_m": trajectory.ate(est, gt), "rpe_t_m": t_rpe, "rpe_r_deg": r_rpe,
-           "median_err_m": float(np.median(err)), "max_err_m": float(err.max()),
+           "mapping": mm,
            "path_m": float(np.sum(np.linalg.norm(np.diff(gt[:, :, 3], axis=0), axis=1)))}
+    out.update(tracked(track_cfg))
+    out["other_trackers"] = [tracked(c) for c in extra_track_cfgs]
     dg.close()
     return out

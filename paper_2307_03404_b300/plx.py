@@ -80,7 +80,7 @@ SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload"
            "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
            "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch",
            "plx_grid_rmsprop", "plx_track_adam_step", "plx_grid_get_config",
-           "plx_grid_set_config", "plx_grid_grow"]
+           "plx_grid_set_config", "plx_grid_grow", "plx_pose_step_lm"]
 
 
 def _load():
@@ -112,6 +112,7 @@ def _load():
                                 P, P, P, D, D, D, D, P, P, P, P],
         "plx_render_batch": [P, C.POINTER(Cameras), C.POINTER(Work), I32, C.POINTER(RenderOpts),
                              P, P, P, P, P, P, P, P],
+        "plx_pose_step_lm": [P, P, P, P, D, D, P, P, P, P],
         "plx_grid_grow": [C.POINTER(GridDesc), P, C.POINTER(Cameras), P, I32, D, P, P],
         "plx_render_backward_pose_noalloc": [C.POINTER(GridDesc), P, P, C.POINTER(Cameras), I32,
                                              C.POINTER(Rays), C.POINTER(RenderOpts), P, P, P, P,
@@ -351,6 +352,20 @@ def pose_step(JtWJ, JtWr, pose, damping=0.0, xi_out=None, status=None, stream=No
     """plx_pose_step: pose (device float64 [12] view) <- exp(xi^) pose."""
     _check(_lib.plx_pose_step(_ptr(JtWJ), _ptr(JtWr), float(damping), _ptr(pose), _ptr(xi_out),
                               _ptr(status), _stream(stream)))
+
+
+def lm_state():
+    """Zeroed state for plx_pose_step_lm."""
+    return torch.zeros(64, device="cuda", dtype=torch.float64)
+
+
+def pose_step_lm(JtWJ, JtWr, loss, state, pose, lambda_init=1e-3, factor=10.0, xi_out=None,
+                 status=None, stream=None):
+    """plx_pose_step_lm: Gauss-Newton with Marquardt damping, accept/reject on
+    the loss; pose (device float64 [12] view) updated in place."""
+    _check(_lib.plx_pose_step_lm(_ptr(JtWJ), _ptr(JtWr), _ptr(loss), _ptr(state),
+                                 float(lambda_init), float(factor), _ptr(pose), _ptr(xi_out),
+                                 _ptr(status), _stream(stream)))
 
 
 def render_batch(grid: Grid, cams: CameraSet, work, opts, rgb_target, depth_target, grad=None,

@@ -277,6 +277,67 @@ def test_pose_step_matches_oracle():
     np.testing.assert_array_equal(pose2.cpu().numpy().reshape(3, 4), T0)
 
 
+def test_pose_step_lm_matches_oracle_sequence():
+    """A sequence of Levenberg-Marquardt calls with losses going down and up
+    (accept, reject and restore, accept) against the oracle's, call by call."""
+    rng = np.random.default_rng(21)
+    T = scenes.look_at((1.0, 0.4, -2.0), (0, 0, 0))
+    st_ref = np.zeros(64)
+    st = torch.zeros(64, device="cuda", dtype=torch.float64)
+    pose = dev(T.reshape(12), torch.float64)
+    xi = torch.empty(6, device="cuda", dtype=torch.float64)
+    status = torch.empty(1, device="cuda", dtype=torch.int32)
+    T_ref = T.copy()
+    statuses = []
+    for k, L in enumerate([1.0, 0.8, 0.9, 0.95, 0.5, 0.5, 0.7, 0.2]):
+        A = rng.standard_normal((9, 6))
+        H = A.T @ A + 0.05 * np.eye(6)
+        b = 0.1 * rng.standard_normal(6)
+        T_ref, xi_ref, s_ref = oracle.pose_step_lm(H, b, L, st_ref, T_ref, 1e-2, 4.0)
+        plx.pose_step_lm(dev(H, torch.float64), dev(b, torch.float64),
+                         dev(np.array([L, 10.0]), torch.float64), st, pose, 1e-2, 4.0,
+                         xi_out=xi, status=status)
+        torch.cuda.synchronize()
+        assert status.item() == s_ref
+        statuses.append(s_ref)
+        np.testing.assert_allclose(xi.cpu().numpy(), xi_ref, rtol=1e-11, atol=1e-15)
+        np.testing.assert_allclose(pose.cpu().numpy().reshape(3, 4), T_ref, atol=1e-13)
+        np.testing.assert_allclose(st.cpu().numpy(), st_ref, rtol=1e-11, atol=1e-15)
+    assert 0 in statuses and 2 in statuses
+
+
+def test_lm_tracking_loop_in_a_cuda_graph_converges(sphere):
+    """The damped loop (pose Jacobian + LM step) in one CUDA graph."""
+    g, cam, _, opts = sphere
+    opts = dict(opts, depth_is_z=False)
+    ref_t = oracle.render(g, [cam], opts)
+    T0 = scenes.perturb_pose(cam.T_wc, 0.03, 2.0, np.random.default_rng(9))
+    case = GpuCase(g, [cam.with_pose(T0)])
+    o = plx.opts_from_dict(opts)
+    rgb_t, depth_t = dev(ref_t.rgb), dev(ref_t.depth)
+    H = torch.empty(6, 6, device="cuda", dtype=torch.float64)
+    b = torch.empty(6, device="cuda", dtype=torch.float64)
+    loss = torch.empty(2, device="cuda", dtype=torch.float64)
+    st = plx.lm_state()
+    pose = case.cams.poses[0]
+    plx.render_backward_pose(case.grid, case.cams, 0, o, rgb_t, depth_t, out=(H, b, loss))
+    plx.pose_step_lm(H, b, loss, st, pose)
+    torch.cuda.synchronize()
+    pose.copy_(dev(T0.reshape(12), torch.float64))
+    st.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        for _ in range(60):
+            plx.render_backward_pose(case.grid, case.cams, 0, o, rgb_t, depth_t, out=(H, b, loss))
+            plx.pose_step_lm(H, b, loss, st, pose)
+    graph.replay()
+    torch.cuda.synchronize()
+    T = pose.cpu().numpy().reshape(3, 4)
+    assert np.abs(T - cam.T_wc).max() < 1e-4 * np.abs(T0 - cam.T_wc).max()
+
+
 def test_tracking_loop_in_a_cuda_graph_converges(sphere):
     """100 GN iterations (pose Jacobian + step) captured in one CUDA graph
     bring a 3 cm / 2 deg perturbed pose back to the rendering pose."""

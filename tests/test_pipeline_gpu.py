@@ -15,7 +15,8 @@ def test_short_sequence_maps_and_tracks():
     sc = scenes.room_scene(128, 0.1, 20, 1002)
     out = pipeline.run(sc, n_frames=60, span=0.06, map_every=10,
                        map_cfg=pipeline.MapConfig(iters=300, rays_per_step=1 << 17),
-                       track_cfg=pipeline.TrackConfig(iters=150, n_rays=2048))
+                       track_cfg=pipeline.TrackConfig(iters=150, n_rays=2048),
+                       extra_track_cfgs=[pipeline.TrackConfig(method="lm", lm_iters=10)])
     assert out["keyframes"] == 6 and out["allocated"] > 0
     first, last = out["map_loss_first_last"]
     assert last < 0.05 * first
@@ -24,3 +25,5 @@ def test_short_sequence_maps_and_tracks():
     assert out["median_err_m"] < 0.02       # 128^3 over 6.4 m: 5 cm voxels
     assert out["max_err_m"] < 0.1
     assert np.isfinite(out["ate_m"])
+    lm = out["other_trackers"][0]
+    assert lm["median_err_m"] < 0.02 and lm["max_err_m"] < 0.1
