@@ -370,24 +370,33 @@ plx_status plx_grid_grow(const plx_grid_desc *desc, int32_t *links,
 /* Launch choices of a grid's kernels (the paper has none; they do not change
  * any result). block_shift: the empty-space map marks blocks of
  * 2^block_shift cells per axis (1..6); rays jump over blocks without an
- * allocated vertex. *_blocks: each ray kernel is compiled for 1 or 2
+ * allocated vertex. fine_skip: a second level inside non-empty blocks (blocks
+ * of 2 cells per axis), per kernel: bit 0 forward, 1 grid adjoint, 2 pose
+ * Jacobian, 3 batched launch (PLX_FINE_*). *_blocks: each ray kernel is compiled for 1 or 2
  * resident blocks of 256 threads per SM (a register budget of 255 or 128 per
  * thread): forward, grid adjoint, pose Jacobian, batched launch. Defaults are
  * the best measured on B300 for room-scale grids; the Python autotuner times
  * the alternatives on a caller's workload. */
+#define PLX_FINE_FORWARD 1
+#define PLX_FINE_ADJOINT 2
+#define PLX_FINE_POSE 4
+#define PLX_FINE_BATCH 8
+
 typedef struct {
   int32_t block_shift;
   int32_t forward_blocks;
   int32_t adjoint_blocks;
   int32_t pose_blocks;
   int32_t batch_blocks;
+  int32_t fine_skip;
 } plx_launch_config;
 
 /* Current launch choices of a grid (HOST out). */
 plx_status plx_grid_get_config(const plx_grid *grid, plx_launch_config *out);
 
-/* Sets the launch choices. A new block_shift rebuilds the empty-space map
- * (allocates, synchronises `stream`); otherwise nothing runs on the device.
+/* Sets the launch choices. A new block_shift or fine_skip rebuilds the
+ * empty-space maps (allocates, synchronises `stream`); otherwise nothing runs
+ * on the device.
  * Errors: PLX_EINVAL (out of range), PLX_ENOMEM, PLX_ECUDA. */
 plx_status plx_grid_set_config(plx_grid *grid, const plx_launch_config *config,
                                void *stream);

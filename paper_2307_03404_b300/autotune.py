@@ -20,6 +20,12 @@ import torch
 from . import plx
 
 SHIFTS = (2, 3, 4)
+FINE_FORWARD, FINE_ADJOINT, FINE_POSE, FINE_BATCH = 1, 2, 4, 8
+
+
+def _fine(bit):
+    """Candidates of fine_skip that toggle one kernel's bit."""
+    return lambda cur: [cur | bit, cur & ~bit]
 BLOCKS = (1, 2)
 
 
@@ -55,6 +61,8 @@ def _descend(grid, fn, fields, reps, log):
     best = _time(fn, reps)
     log.append((dict(best_cfg), best))
     for name, cands in fields:
+        if callable(cands):
+            cands = cands(best_cfg[name])
         for v in cands:
             if v == best_cfg[name]:
                 continue
@@ -98,7 +106,7 @@ def _store(key, entry, cache):
 
 def tune_mapping(grid, cams, opts, rgb_target, depth_target, rays=None, reps=3, cache=None,
                  use_cache=True):
-    """Tune block_shift, forward_blocks and adjoint_blocks on one mapping step
+    """Tune block_shift, fine_skip, forward_blocks and adjoint_blocks on one mapping step
     (forward + adjoint) of these rays. Returns dict(config, ms, trials)."""
     n = cams.n_pixels() if rays is None else int(rays[1].shape[0])
     key = _key(grid, "mapping", n)
@@ -116,7 +124,8 @@ def tune_mapping(grid, cams, opts, rgb_target, depth_target, rays=None, reps=3, 
                                  fw["depth"], rays=rays, grad=grad, loss=loss)
 
     log = []
-    cfg, ms = _descend(grid, step, [("block_shift", SHIFTS), ("adjoint_blocks", BLOCKS),
+    cfg, ms = _descend(grid, step, [("block_shift", SHIFTS), ("fine_skip", _fine(FINE_FORWARD)),
+                                    ("fine_skip", _fine(FINE_ADJOINT)), ("adjoint_blocks", BLOCKS),
                                     ("forward_blocks", BLOCKS)], reps, log)
     entry = {"config": cfg, "ms": ms, "trials": [[c, t] for c, t in log]}
     _store(key, entry, cache)
@@ -125,7 +134,7 @@ def tune_mapping(grid, cams, opts, rgb_target, depth_target, rays=None, reps=3, 
 
 def tune_tracking(grid, cams, cam, opts, rgb_target, depth_target, reps=3, cache=None,
                   use_cache=True):
-    """Tune pose_blocks (and block_shift) on one pose-Jacobian launch."""
+    """Tune pose_blocks (and block_shift, fine_skip) on one pose-Jacobian launch."""
     key = _key(grid, "tracking", cams.n_pixels(cam))
     if use_cache:
         hit = _lookup(grid, key, cache)
@@ -139,7 +148,8 @@ def tune_tracking(grid, cams, cam, opts, rgb_target, depth_target, reps=3, cache
         plx.render_backward_pose(grid, cams, cam, opts, rgb_target, depth_target, out=out)
 
     log = []
-    cfg, ms = _descend(grid, step, [("pose_blocks", BLOCKS), ("block_shift", SHIFTS)], reps, log)
+    cfg, ms = _descend(grid, step, [("pose_blocks", BLOCKS), ("block_shift", SHIFTS),
+                                    ("fine_skip", _fine(FINE_POSE))], reps, log)
     entry = {"config": cfg, "ms": ms, "trials": [[c, t] for c, t in log]}
     _store(key, entry, cache)
     return dict(entry, cached=False)
@@ -147,7 +157,7 @@ def tune_tracking(grid, cams, cam, opts, rgb_target, depth_target, reps=3, cache
 
 def tune_batch(grid, cams, work, opts, rgb_target, depth_target, reps=2, cache=None,
                use_cache=True):
-    """Tune batch_blocks (and block_shift) on one batched launch."""
+    """Tune batch_blocks (and block_shift, fine_skip) on one batched launch."""
     n = sum(cams.n_pixels(c) for c, _ in work)
     key = _key(grid, f"batch{len(work)}", n)
     if use_cache:
@@ -160,7 +170,8 @@ def tune_batch(grid, cams, work, opts, rgb_target, depth_target, reps=2, cache=N
         plx.render_batch(grid, cams, work, opts, rgb_target, depth_target, grad=grad)
 
     log = []
-    cfg, ms = _descend(grid, step, [("batch_blocks", BLOCKS), ("block_shift", SHIFTS)], reps, log)
+    cfg, ms = _descend(grid, step, [("batch_blocks", BLOCKS), ("block_shift", SHIFTS),
+                                    ("fine_skip", _fine(FINE_BATCH))], reps, log)
     entry = {"config": cfg, "ms": ms, "trials": [[c, t] for c, t in log]}
     _store(key, entry, cache)
     return dict(entry, cached=False)

@@ -58,6 +58,8 @@ struct plx_grid {
   void* rec = nullptr;
   uint8_t* blk = nullptr;         // empty-space blocks (null: none)
   int nb[3] = {0, 0, 0};
+  uint8_t* fblk = nullptr;        // second level, blocks of 2^kFineShift cells
+  int fnb[3] = {0, 0, 0};
   int rec_bytes = 0;
   char* ws = nullptr;
   int max_pose_blocks = 0;        // partials the workspace holds (max over variants)
@@ -197,9 +199,10 @@ static unsigned grid_stride_blocks(int64_t n, int num_sms) {
   return (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
-// (Re)builds the empty-space map of `g` for blocks of 2^shift cells.
-static cudaError_t build_block_map(plx_grid* g, int shift, cudaStream_t s) {
-  int nb[3];
+// Builds a map of blocks of 2^shift cells (1 = some cell has an allocated
+// corner) into freshly allocated memory.
+static cudaError_t make_block_map(const plx_grid* g, int shift, cudaStream_t s, uint8_t** out,
+                                  int nb[3]) {
   for (int a = 0; a < 3; ++a) nb[a] = ((g->desc.res[a] - 1) + (1 << shift) - 1) >> shift;
   const size_t bytes = (size_t)nb[0] * nb[1] * nb[2];
   uint8_t* blk = nullptr;
@@ -218,9 +221,29 @@ static cudaError_t build_block_map(plx_grid* g, int shift, cudaStream_t s) {
     cudaFree(blk);
     return e;
   }
+  *out = blk;
+  return cudaSuccess;
+}
+
+// (Re)builds the empty-space maps of `g`: blocks of 2^shift cells, and the
+// second level of 2^kFineShift cells when `fine` is set.
+static cudaError_t build_block_map(plx_grid* g, int shift, int fine, cudaStream_t s) {
+  int nb[3], fnb[3] = {0, 0, 0};
+  uint8_t *blk = nullptr, *fblk = nullptr;
+  cudaError_t e = make_block_map(g, shift, s, &blk, nb);
+  if (e == cudaSuccess && fine) e = make_block_map(g, kFineShift, s, &fblk, fnb);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    return e;
+  }
   cudaFree(g->blk);
+  cudaFree(g->fblk);
   g->blk = blk;
-  for (int a = 0; a < 3; ++a) g->nb[a] = nb[a];
+  g->fblk = fblk;
+  for (int a = 0; a < 3; ++a) {
+    g->nb[a] = nb[a];
+    g->fnb[a] = fnb[a];
+  }
   g->cfg.block_shift = shift;
   return cudaSuccess;
 }
@@ -267,6 +290,7 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
     cudaFree(g->links);
     cudaFree(g->rec);
     cudaFree(g->blk);
+    cudaFree(g->fblk);
     cudaFree(g->ws);
     delete g;
     return st;
@@ -285,6 +309,7 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
   g->cfg.adjoint_blocks = kDefaultBwdBlocks;
   g->cfg.pose_blocks = kDefaultPoseBlocks;
   g->cfg.batch_blocks = kDefaultBatchBlocks;
+  g->cfg.fine_skip = kDefaultFineSkip;
   apply_config(g);
   const size_t ws_bytes = sizeof(Workspace) +
                           ((size_t)g->max_pose_blocks + PLX_MAX_CAMERAS) * 32 * sizeof(double);
@@ -311,7 +336,7 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cleanup(fail(PLX_ECUDA, "grid_create: %s", cudaGetErrorString(e)));
   if (err) return cleanup(fail(PLX_EINVAL, "grid_create: a link is outside [-1, n_alloc)"));
-  e = build_block_map(g, kDefaultBlkShift, s);
+  e = build_block_map(g, kDefaultBlkShift, kDefaultFineSkip != 0, s);
   if (e != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA,
                         "grid_create: empty-space map: %s", cudaGetErrorString(e)));
@@ -349,6 +374,7 @@ plx_status plx_grid_destroy(plx_grid* g) {
   cudaFree(g->links);
   cudaFree(g->rec);
   cudaFree(g->blk);
+  cudaFree(g->fblk);
   cudaFree(g->ws);
   delete g;
   if (e != cudaSuccess) return fail(PLX_ECUDA, "grid_destroy: %s", cudaGetErrorString(e));
@@ -371,9 +397,11 @@ plx_status plx_grid_check(const plx_grid* g, void* stream) {
 }  // extern "C"
 
 // ------------------------------------------------------------ call set-up
+// fine_bit: the PLX_FINE_* bit of the kernel about to run (its second-level
+// empty-space map is used if that bit is set in the grid's fine_skip).
 static plx_status build_common(const char* what, const plx_grid* g, const plx_cameras* cams,
                                const plx_rays* rays, const plx_render_opts* o, int32_t fixed_cam,
-                               Common& P) {
+                               int fine_bit, Common& P) {
   if (!g || !cams || !rays || !o) return fail(PLX_EINVAL, "%s: null argument", what);
   if (cams->n_cams < 1 || cams->n_cams > PLX_MAX_CAMERAS)
     return fail(PLX_EINVAL, "%s: n_cams %d out of [1, %d]", what, cams->n_cams, PLX_MAX_CAMERAS);
@@ -394,6 +422,9 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
   P.g.nbx = g->nb[0];
   P.g.nby = g->nb[1];
   P.g.blk_shift = g->cfg.block_shift;
+  P.g.fblk = (g->cfg.fine_skip & fine_bit) ? g->fblk : nullptr;
+  P.g.fnbx = g->fnb[0];
+  P.g.fnby = g->fnb[1];
   P.g.rx = g->desc.res[0];
   P.g.ry = g->desc.res[1];
   P.g.rz = g->desc.res[2];
@@ -481,7 +512,7 @@ plx_status plx_render_forward(const plx_grid* g, const plx_cameras* cams, const 
                               const plx_render_opts* opts, float* rgb_out, float* depth_out,
                               float* state_out, int32_t* counts_out, void* stream) {
   Common P;
-  plx_status st = build_common("render_forward", g, cams, rays, opts, -1, P);
+  plx_status st = build_common("render_forward", g, cams, rays, opts, -1, PLX_FINE_FORWARD, P);
   if (st != PLX_OK) return st;
   if (P.ct.n_rays > 0 && (!rgb_out || !depth_out))
     return fail(PLX_EINVAL, "render_forward: null rgb_out or depth_out");
@@ -496,7 +527,7 @@ plx_status plx_render_backward_grid(const plx_grid* g, const plx_cameras* cams,
                                     const float* rgb, const float* depth, float* grad,
                                     double* loss_out, void* stream) {
   Common P;
-  plx_status st = build_common("render_backward_grid", g, cams, rays, opts, -1, P);
+  plx_status st = build_common("render_backward_grid", g, cams, rays, opts, -1, PLX_FINE_ADJOINT, P);
   if (st != PLX_OK) return st;
   if (P.ct.n_rays > 0 && (!rgb_target || !depth_target || !rgb || !depth || !grad))
     return fail(PLX_EINVAL, "render_backward_grid: null array argument");
@@ -514,7 +545,7 @@ plx_status plx_render_backward_pose(const plx_grid* g, const plx_cameras* cams, 
                                     double* JtWJ, double* JtWr, double* loss, void* stream) {
   if (cam < 0) return fail(PLX_EINVAL, "render_backward_pose: cam < 0");
   Common P;
-  plx_status st = build_common("render_backward_pose", g, cams, rays, opts, cam, P);
+  plx_status st = build_common("render_backward_pose", g, cams, rays, opts, cam, PLX_FINE_POSE, P);
   if (st != PLX_OK) return st;
   if (!JtWJ || !JtWr || !loss) return fail(PLX_EINVAL, "render_backward_pose: null output");
   if (P.ct.n_rays > 0 && (!rgb_target || !depth_target))
@@ -567,8 +598,11 @@ extern "C" plx_status plx_grid_set_config(plx_grid* g, const plx_launch_config* 
   for (int i = 0; i < 4; ++i)
     if (v[i] != 1 && v[i] != 2)
       return fail(PLX_EINVAL, "%s: blocks per SM must be 1 or 2", what);
-  if (c->block_shift != g->cfg.block_shift) {
-    const cudaError_t e = build_block_map(g, c->block_shift, (cudaStream_t)stream);
+  if (c->fine_skip < 0 || c->fine_skip > 15)
+    return fail(PLX_EINVAL, "%s: fine_skip must be a mask of PLX_FINE_* bits", what);
+  if (c->block_shift != g->cfg.block_shift || (c->fine_skip != 0) != (g->cfg.fine_skip != 0)) {
+    const cudaError_t e =
+        build_block_map(g, c->block_shift, c->fine_skip != 0, (cudaStream_t)stream);
     if (e != cudaSuccess)
       return fail(e == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA, "%s: %s", what,
                   cudaGetErrorString(e));
@@ -595,7 +629,7 @@ extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cam
   Common P;
   if (opts && (opts->pose_flags & PLX_POSE_VIEW_DIR))
     return fail(PLX_EINVAL, "%s: the view-direction variant is not in the batched launch", what);
-  plx_status st = build_common(what, g, cams, &dense, opts, -1, P);
+  plx_status st = build_common(what, g, cams, &dense, opts, -1, PLX_FINE_BATCH, P);
   if (st != PLX_OK) return st;
   const CamTable base = P.ct;
   int n_map = 0, n_track = 0;
@@ -723,7 +757,7 @@ extern "C" plx_status plx_track_adam_step(const plx_grid* g, const plx_cameras* 
   dense.cam_id = nullptr;
   dense.pixel = nullptr;
   Common P;
-  plx_status st = build_common(what, g, cams, &dense, opts, cam, P);
+  plx_status st = build_common(what, g, cams, &dense, opts, cam, PLX_FINE_POSE, P);
   if (st != PLX_OK) return st;
   P.ct.dense = 0;
   P.ct.n_rays = n_rays;
@@ -821,9 +855,10 @@ extern "C" plx_status plx_render_backward_pose_noalloc(
   view.rec_bytes = record_bytes(desc->storage);
   view.ws = scratch;
   view.cfg.block_shift = kDefaultBlkShift;  // unused: the view has no empty-space map
+  view.cfg.fine_skip = 0;
   for (int a = 0; a < 3; ++a) view.inv_h[a] = (double)(desc->res[a] - 1) / (desc->hi[a] - desc->lo[a]);
   Common P;
-  st = build_common(what, &view, cams, rays, opts, cam, P);
+  st = build_common(what, &view, cams, rays, opts, cam, PLX_FINE_POSE, P);
   if (st != PLX_OK) return st;
   if (!JtWJ || !JtWr || !loss) return fail(PLX_EINVAL, "%s: null output", what);
   if (P.ct.n_rays > 0 && (!rgb_target || !depth_target))

@@ -93,6 +93,8 @@ constexpr int kDefaultFwdBlocks = 1;
 constexpr int kDefaultBwdBlocks = 2;
 constexpr int kDefaultPoseBlocks = 2;
 constexpr int kDefaultBatchBlocks = 1;
+constexpr int kDefaultFineSkip = PLX_FINE_ADJOINT | PLX_FINE_POSE | PLX_FINE_BATCH;
+constexpr int kFineShift = 1;         // second-level empty-space blocks: 2^1 cells per axis
 
 struct GridView {
   const int32_t* links;           // [rz][ry][rx]
@@ -103,6 +105,8 @@ struct GridView {
   int32_t n_alloc;
   int32_t nbx, nby;
   int32_t blk_shift;              // blocks of 2^blk_shift cells per axis
+  const uint8_t* fblk;            // second level: blocks of 2^3 cells (null: none)
+  int32_t fnbx, fnby;
   double lo[3];                   // box of the vertices
   double hi[3];
   double inv_h[3];                // 1 / spacing
@@ -490,23 +494,29 @@ __device__ __forceinline__ bool load_cell(const GridView& g, int ix, int iy, int
 // Empty-space skipping. Samples whose cell lies in a block without any
 // allocated vertex contribute exactly nothing (sigma = 0 there), so the march
 // may jump over them; later samples keep their own index k, so nothing else
-// changes. Returns true if cell (ix, iy, iz) lies in such a block.
-__device__ __forceinline__ bool block_empty(const GridView& g, int ix, int iy, int iz) {
-  if (!g.blk) return false;
+// changes. Two levels: blocks of 2^blk_shift cells, and inside a non-empty one
+// blocks of 2 cells per axis. Returns the shift (log2 of the block size) of
+// an empty block holding cell (ix, iy, iz), or -1 if there is none.
+__device__ __forceinline__ int empty_block_shift(const GridView& g, int ix, int iy, int iz) {
+  if (!g.blk) return -1;
   const int sh = g.blk_shift;
-  const int bx = ix >> sh, by = iy >> sh, bz = iz >> sh;
-  return __ldg(g.blk + ((int64_t)bz * g.nby + by) * g.nbx + bx) == 0;
+  if (__ldg(g.blk + ((int64_t)(iz >> sh) * g.nby + (iy >> sh)) * g.nbx + (ix >> sh)) == 0)
+    return sh;
+  if (g.fblk && __ldg(g.fblk + ((int64_t)(iz >> kFineShift) * g.fnby + (iy >> kFineShift)) * g.fnbx +
+                      (ix >> kFineShift)) == 0)
+    return kFineShift;
+  return -1;
 }
 
-// Index of the first sample that may lie outside the block of cell
-// (ix, iy, iz), never past it: the exit parameter along each axis is exact to
+// Index of the first sample that may lie outside the empty block of 2^sh
+// cells per axis holding cell (ix, iy, iz) (conservative: never past the
+// first sample outside). Per axis the ray leaves the block at grid
+// coordinate (block face) - b = k s, solved for k in FP32: the error is below
 // ~1e-6 samples (the distance to the block face is a Sterbenz-exact
 // difference), and 0.01 samples of margin keep the jump on the safe side.
 // Always > k.
-__device__ __forceinline__ int block_exit(const GridView& g, const RayF& r, int ix, int iy, int iz,
-                                          int k) {
+__device__ __forceinline__ int block_exit(const RayF& r, int ix, int iy, int iz, int k, int sh) {
   const int c[3] = {ix, iy, iz};
-  const int sh = g.blk_shift;
   float kmin = 3.0e38f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {

@@ -27,9 +27,10 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
     sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
     if (ix != cx || iy != cy || iz != cz) {
       cx = ix; cy = iy; cz = iz;
-      if (block_empty(P.g, ix, iy, iz)) {
+      const int esh = empty_block_shift(P.g, ix, iy, iz);
+      if (esh >= 0) {
         empty = true;
-        k = block_exit(P.g, r, ix, iy, iz, k) - 1;
+        k = block_exit(r, ix, iy, iz, k, esh) - 1;
         continue;
       }
       empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
@@ -144,7 +145,8 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
     sample_axis(r.bh[1], r.bl[1], r.sh[1], r.sl[1], kf, rm2y, iy, fy);
     sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
     if (ix != cx || iy != cy || iz != cz) {
-      const bool skip = block_empty(P.g, ix, iy, iz);
+      const int esh = empty_block_shift(P.g, ix, iy, iz);
+      const bool skip = esh >= 0;
       if (dirty) {
         const int dx = ix - cx, dy = iy - cy, dz = iz - cz;
         int step = -1;  // face-adjacent step: 0/1 = +x/-x, 2/3 = +y/-y, 4/5 = +z/-z
@@ -167,7 +169,7 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
       cx = ix; cy = iy; cz = iz;
       if (skip) {
         empty = true;
-        k = block_exit(P.g, r, ix, iy, iz, k) - 1;
+        k = block_exit(r, ix, iy, iz, k, esh) - 1;
         continue;
       }
       empty = load_cell_smem<STORE>(P.g, ix, iy, iz, Y, l, sc);

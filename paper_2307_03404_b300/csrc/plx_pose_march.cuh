@@ -89,9 +89,10 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
         if (!empty) dir_flush<STORE>(P.g, l, Ac, r.dir, A.G);
       }
       cx = ix; cy = iy; cz = iz;
-      if (block_empty(P.g, ix, iy, iz)) {
+      const int esh = empty_block_shift(P.g, ix, iy, iz);
+      if (esh >= 0) {
         empty = true;
-        k = block_exit(P.g, r, ix, iy, iz, k) - 1;
+        k = block_exit(r, ix, iy, iz, k, esh) - 1;
         continue;
       }
       empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);

@@ -26,6 +26,7 @@ ACT_SIGMOID, ACT_IDENTITY = 0, 1
 MAX_CAMERAS = 128
 GRAD_STRIDE = 32
 POSE_VIEW_DIR = 1
+FINE_FORWARD, FINE_ADJOINT, FINE_POSE, FINE_BATCH = 1, 2, 4, 8
 
 STATUS = {0: "PLX_OK", 1: "PLX_EINVAL", 2: "PLX_ENOMEM", 3: "PLX_ECUDA",
           4: "PLX_EDEVICE_CHECK", 5: "PLX_ETIMEOUT", 6: "PLX_EUNSUPPORTED"}
@@ -66,7 +67,7 @@ WORK_MAP, WORK_TRACK = 0, 1
 class LaunchConfig(C.Structure):
     _fields_ = [("block_shift", C.c_int32), ("forward_blocks", C.c_int32),
                 ("adjoint_blocks", C.c_int32), ("pose_blocks", C.c_int32),
-                ("batch_blocks", C.c_int32)]
+                ("batch_blocks", C.c_int32), ("fine_skip", C.c_int32)]
 
 
 class RenderOpts(C.Structure):
@@ -201,8 +202,8 @@ class Grid:
         return {f: int(getattr(c, f)) for f, _ in LaunchConfig._fields_}
 
     def set_config(self, stream=None, **kw):
-        """Change launch choices (block_shift, forward_blocks, adjoint_blocks,
-        pose_blocks, batch_blocks); results do not change."""
+        """Change launch choices (block_shift, fine_skip, forward_blocks,
+        adjoint_blocks, pose_blocks, batch_blocks); results do not change."""
         cur = self.get_config()
         cur.update({k: int(v) for k, v in kw.items()})
         c = LaunchConfig(**cur)

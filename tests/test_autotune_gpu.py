@@ -22,11 +22,11 @@ def test_every_launch_config_gives_the_oracle_result():
     rp = oracle.pose_jacobian(g, [cam], opts, tg.rgb, tg.depth)
     case = GpuCase(g, [cam])
     assert case.grid.get_config() == dict(block_shift=3, forward_blocks=1, adjoint_blocks=2,
-                                          pose_blocks=2, batch_blocks=1)
-    for shift in (1, 2, 4):
+                                          pose_blocks=2, batch_blocks=1, fine_skip=14)
+    for shift, fine in ((1, 0), (2, 15), (3, 0), (4, 15), (4, 0), (3, 5)):
         for blocks in (1, 2):
             case.grid.set_config(block_shift=shift, forward_blocks=blocks, adjoint_blocks=blocks,
-                                 pose_blocks=blocks)
+                                 pose_blocks=blocks, fine_skip=fine)
             got = case.forward(opts)
             assert rel_err(got["rgb"], ref.rgb) <= 1e-5
             np.testing.assert_array_equal(got["counts"][:, 1], ref.n_alloc)
@@ -40,6 +40,8 @@ def test_every_launch_config_gives_the_oracle_result():
         case.grid.set_config(block_shift=0)
     with pytest.raises(plx.PlxError):
         case.grid.set_config(adjoint_blocks=3)
+    with pytest.raises(plx.PlxError):
+        case.grid.set_config(fine_skip=16)
 
 
 def test_autotuner_picks_and_caches_a_config(tmp_path):
