@@ -148,7 +148,9 @@ const char *plx_version(void);
  *   density DEVICE float [n_alloc]
  *   sh      DEVICE float [n_alloc][27], channel-major (R0..R8, G0..G8, B0..B8)
  * Synchronises `stream`. Errors: PLX_EINVAL (descriptor, or a link out of
- * range), PLX_ENOMEM, PLX_ECUDA. On success *out owns the copy; the caller's
+ * range), PLX_ENOMEM (also, before anything is allocated, when the
+ * environment variable PLX_ALLOC_CAP_BYTES is set below the bytes the grid
+ * needs), PLX_ECUDA. On success *out owns the copy; the caller's
  * arrays may be freed. */
 plx_status plx_grid_create(const plx_grid_desc *desc, const int32_t *links,
                            const float *density, const float *sh, void *stream,

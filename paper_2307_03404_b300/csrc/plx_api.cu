@@ -4,6 +4,7 @@
 // and launches.
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -281,6 +282,17 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
     return fail(PLX_EINVAL, "grid_create: null density or sh");
   const int64_t n_links = (int64_t)desc->res[0] * desc->res[1] * desc->res[2];
   cudaStream_t s = (cudaStream_t)stream;
+  // optional cap on the device memory one grid may take (PLX_ALLOC_CAP_BYTES),
+  // checked before anything is allocated: a way to meet the out-of-memory path
+  // on purpose without exhausting a shared device
+  if (const char* cap_s = std::getenv("PLX_ALLOC_CAP_BYTES")) {
+    const double cap = std::atof(cap_s);
+    const double need = (double)n_links * 4.0 * 1.15 +
+                        (double)(desc->n_alloc > 0 ? desc->n_alloc : 1) * record_bytes(desc->storage);
+    if (cap > 0.0 && need > cap)
+      return fail(PLX_ENOMEM, "grid_create: needs %.0f bytes, over PLX_ALLOC_CAP_BYTES = %.0f",
+                  need, cap);
+  }
 
   plx_grid* g = new plx_grid();
   g->desc = *desc;

@@ -143,6 +143,27 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+_NVTX = os.environ.get("PLX_NVTX") == "1"
+
+
+def _ranged(fn):
+    """With PLX_NVTX=1, wrap an entry point in an NVTX range of its name (for
+    timeline profilers); otherwise return it unchanged."""
+    if not _NVTX:
+        return fn
+    import functools
+
+    @functools.wraps(fn)
+    def wrapper(*a, **kw):
+        torch.cuda.nvtx.range_push("plx." + fn.__name__)
+        try:
+            return fn(*a, **kw)
+        finally:
+            torch.cuda.nvtx.range_pop()
+
+    return wrapper
+
+
 def version() -> str:
     return _lib.plx_version().decode()
 
@@ -299,6 +320,7 @@ def opts_from_dict(d):
 
 
 # ----------------------------------------------------------- entry points
+@_ranged
 def render_forward(grid: Grid, cams: CameraSet, opts, rays=None, state=True, counts=False,
                    out=None, stream=None):
     """plx_render_forward. ``rays`` = (cam_id, pixel) or None (dense).
@@ -316,6 +338,7 @@ def render_forward(grid: Grid, cams: CameraSet, opts, rays=None, state=True, cou
     return out
 
 
+@_ranged
 def render_backward_grid(grid: Grid, cams: CameraSet, opts, rgb_target, depth_target, rgb,
                          depth, rays=None, grad=None, loss=None, stream=None):
     """plx_render_backward_grid. Adds into ``grad`` [n_alloc, 32] (allocated
@@ -332,6 +355,7 @@ def render_backward_grid(grid: Grid, cams: CameraSet, opts, rgb_target, depth_ta
     return grad, loss
 
 
+@_ranged
 def render_backward_pose(grid: Grid, cams: CameraSet, cam: int, opts, rgb_target, depth_target,
                          rays=None, out=None, stream=None):
     """plx_render_backward_pose for camera ``cam``; ``rays`` = pixel list or None.
@@ -349,6 +373,7 @@ def render_backward_pose(grid: Grid, cams: CameraSet, cam: int, opts, rgb_target
     return out
 
 
+@_ranged
 def pose_step(JtWJ, JtWr, pose, damping=0.0, xi_out=None, status=None, stream=None):
     """plx_pose_step: pose (device float64 [12] view) <- exp(xi^) pose."""
     _check(_lib.plx_pose_step(_ptr(JtWJ), _ptr(JtWr), float(damping), _ptr(pose), _ptr(xi_out),
@@ -360,6 +385,7 @@ def lm_state():
     return torch.zeros(64, device="cuda", dtype=torch.float64)
 
 
+@_ranged
 def pose_step_lm(JtWJ, JtWr, loss, state, pose, lambda_init=1e-3, factor=10.0, xi_out=None,
                  status=None, stream=None):
     """plx_pose_step_lm: Gauss-Newton with Marquardt damping, accept/reject on
@@ -369,6 +395,7 @@ def pose_step_lm(JtWJ, JtWr, loss, state, pose, lambda_init=1e-3, factor=10.0, x
                                  _ptr(status), _stream(stream)))
 
 
+@_ranged
 def render_batch(grid: Grid, cams: CameraSet, work, opts, rgb_target, depth_target, grad=None,
                  map_loss=None, out=None, stream=None):
     """plx_render_batch. ``work`` = [(cam, WORK_MAP | WORK_TRACK), ...]; targets
@@ -398,6 +425,7 @@ def render_batch(grid: Grid, cams: CameraSet, work, opts, rgb_target, depth_targ
     return grad, map_loss, out[0][:n_track], out[1][:n_track], out[2][:n_track]
 
 
+@_ranged
 def grid_rmsprop(grid: Grid, grad, state, lr, alpha=0.99, eps=1e-8, zero_grad=True, stream=None,
                  lr_density=None):
     """plx_grid_rmsprop: one RMSProp step on every stored grid value, in place
@@ -408,6 +436,7 @@ def grid_rmsprop(grid: Grid, grad, state, lr, alpha=0.99, eps=1e-8, zero_grad=Tr
                                  float(alpha), float(eps), int(bool(zero_grad)), _stream(stream)))
 
 
+@_ranged
 def grid_grow(res, lo, hi, links: torch.Tensor, n_alloc: int, cams: CameraSet, depth, band,
               depth_is_z=True, n_new=None, stream=None):
     """Grow a link array from observed depth (``plx_grid_grow``): ``links`` (a
@@ -434,6 +463,7 @@ def adam_state():
     return torch.zeros(20, device="cuda", dtype=torch.float64)
 
 
+@_ranged
 def track_adam_step(grid: Grid, cams: CameraSet, cam: int, opts, n_rays, seed, rgb_target,
                     depth_target, state, lr, beta1=0.9, beta2=0.999, eps=1e-8, out=None,
                     stream=None):

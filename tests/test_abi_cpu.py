@@ -133,3 +133,48 @@ def test_grid_grow_argument_errors(lib):
     d.n_alloc = -3
     assert lib.plx_grid_grow(C.byref(d), x, C.byref(cams), x, 1, 2.0, x, None) == 1
     assert b"n_alloc" in lib.plx_last_error()
+
+
+def test_pose_step_lm_argument_errors(lib):
+    from paper_2307_03404_b300 import plx
+
+    lib = plx._lib
+    x = (C.c_double * 64)()
+    assert lib.plx_pose_step_lm(None, x, x, x, 1e-3, 10.0, x, None, None, None) == 1
+    assert b"null" in lib.plx_last_error()
+    assert lib.plx_pose_step_lm(x, x, x, x, -1.0, 10.0, x, None, None, None) == 1
+    assert b"lambda_init" in lib.plx_last_error()
+    assert lib.plx_pose_step_lm(x, x, x, x, 1e-3, 1.0, x, None, None, None) == 1
+    assert lib.plx_pose_step_lm(x, x, x, x, 1e-3, float("inf"), x, None, None, None) == 1
+
+
+def test_set_config_and_opts_flags_are_validated_on_the_host(lib):
+    from paper_2307_03404_b300 import plx
+
+    lib = plx._lib
+    c = plx.LaunchConfig(3, 1, 2, 2, 1, 14)
+    assert lib.plx_grid_set_config(None, C.byref(c), None) == 1
+    o = plx.make_opts(0.1)
+    o.pose_flags = 2
+    assert lib.plx_render_forward(None, None, None, C.byref(o), None, None, None, None, None) == 1
+
+
+def test_allocation_cap_reports_out_of_memory_before_allocating(lib):
+    """Host-side fault injection: with PLX_ALLOC_CAP_BYTES below what a grid
+    needs, plx_grid_create fails with PLX_ENOMEM before any device call (so
+    this runs without a GPU)."""
+    import subprocess
+    import sys
+
+    code = (
+        "import ctypes as C\n"
+        "from paper_2307_03404_b300 import plx\n"
+        "d = plx.GridDesc(); d.res[:] = [64, 64, 64]; d.hi[:] = [1, 1, 1]; d.n_alloc = 1000\n"
+        "x = (C.c_float * 16)(); h = C.c_void_p()\n"
+        "st = plx._lib.plx_grid_create(C.byref(d), x, x, x, None, C.byref(h))\n"
+        "print(st, plx._lib.plx_last_error().decode())\n")
+    env = dict(os.environ, PLX_ALLOC_CAP_BYTES="100000")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         cwd=ROOT, timeout=300)
+    st, msg = out.stdout.strip().split(" ", 1)
+    assert int(st) == 2 and "PLX_ALLOC_CAP_BYTES" in msg

@@ -104,6 +104,38 @@ def test_forward_edge_cases():
     np.testing.assert_allclose(got["rgb"][:, 2], 0.9, rtol=1e-7)
 
 
+def test_axis_aligned_rays_on_grid_planes():
+    """Rays exactly along the grid axes, starting on vertex planes (direction
+    components exactly 0, sample positions exactly on cell faces): forward,
+    adjoint and pose system against the oracle, sample counts bit-exact."""
+    g = scenes.tiny_grid(9, seed=4, alloc_frac=0.8)
+    h = (g.hi - g.lo) / (np.array(g.res) - 1)
+    cams = []
+    for R_ in (np.eye(3), np.array([[0.0, 0, 1], [0, 1, 0], [-1, 0, 0]]),
+               np.array([[1.0, 0, 0], [0, 0, -1], [0, 1, 0]])):
+        T = np.zeros((3, 4))
+        T[:, :3] = R_
+        T[:, 3] = g.lo + h * np.array([4.0, 3.0, 2.0]) - 3.0 * R_[:, 2]   # a vertex, 3 back
+        # 5x5 pixels with the centre pixel's ray exactly on the optical axis
+        cams.append(scenes.Camera(6.0, 6.0, 2.5, 2.5, 5, 5, T))
+    opts = dict(step=0.5 * h[0], lambda_d=0.6, depth_is_z=False, bg=(0.2, 0.1, 0.3))
+    case = GpuCase(g, cams)
+    got = case.forward(opts)
+    ref = oracle.render(g, cams, opts)
+    assert rel_err(got["rgb"], ref.rgb) <= TOL_FWD
+    assert rel_err(got["depth"], ref.depth) <= TOL_FWD
+    np.testing.assert_array_equal(got["counts"][:, 0], ref.n_marched)
+    np.testing.assert_array_equal(got["counts"][:, 1], ref.n_alloc)
+    rgb_t = np.clip(ref.rgb + 0.05, 0, 1).astype(np.float32)
+    depth_t = (ref.depth * 1.02 + 0.01).astype(np.float32)
+    gd, gs, _, loss = case.backward_grid(opts, rgb_t, depth_t)
+    rg = oracle.grad_grid(g, cams, opts, rgb_t, depth_t)
+    assert norm_err(gd, rg.grad_density) <= TOL_GRAD and norm_err(gs, rg.grad_sh) <= TOL_GRAD
+    H, b, _ = case.backward_pose(opts, 1, rgb_t[25:50], depth_t[25:50])
+    rp = oracle.pose_jacobian(g, [cams[1]], opts, rgb_t[25:50], depth_t[25:50])
+    assert norm_err(H, rp.H) <= TOL_GRAD and norm_err(b, rp.b) <= TOL_GRAD
+
+
 def test_bad_ray_list_sets_the_device_error_word():
     cams = tiny_cams()
     case = GpuCase(scenes.tiny_grid(5, seed=2), cams)
