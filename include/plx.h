@@ -21,10 +21,11 @@
  *     plx_render_opts) are HOST memory, read during the call only.
  *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
  *     stream. Every call is asynchronous on its stream, except
- *     plx_grid_create / plx_grid_destroy / plx_grid_check, which synchronise.
- *     No call synchronises the device or allocates memory except those three,
- *     so the render, backward and pose-step calls can be captured in a CUDA
- *     graph.
+ *     plx_grid_create / plx_grid_destroy / plx_grid_check, which synchronise,
+ *     and plx_grid_set_config when it rebuilds the empty-space maps. Besides
+ *     those, only plx_grid_grow allocates (stream-ordered scratch), so the
+ *     render, backward, pose-step and optimiser calls can be captured in a
+ *     CUDA graph.
  *   - A grid handle owns scratch memory: calls that use one handle must not
  *     run concurrently on different streams.
  *
