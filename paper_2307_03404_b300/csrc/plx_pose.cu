@@ -48,7 +48,7 @@ k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_
     float dz = 0.f;
     if (id.valid) dz = __ldg(depth_t + id.out);
     if (id.valid && depth_valid(dz))
-      pose_ray_values<STORE, DIRT>(P, r, rgb_t + 3 * id.out, dz, v);
+      pose_ray_values<STORE, DIRT, true>(P, r, rgb_t + 3 * id.out, dz, v);
     acc += warp_reduce_scatter(v, lane);
   }
   red[warp][lane] = acc;

@@ -60,7 +60,10 @@ __device__ __forceinline__ void dir_flush(const GridView& g, const int32_t l[8],
   }
 }
 
-template <int STORE, bool DIRT = false>
+// SMEM: the cell's corner cache lives in shared memory (slot s of this
+// thread at sc[s * kBlock], as in the adjoint), so registers hold the corner
+// values only while a sample uses them.
+template <int STORE, bool DIRT = false, bool SMEM = false>
 __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const float Y[9],
                                            float C[3], float& D, float& T, PoseAcc& A) {
   const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
@@ -68,7 +71,12 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
   int cx = -1, cy = -1, cz = -1;
   bool empty = true;
   int32_t l[8];
-  float cs[8], cc[8][3];
+  float cs_r[SMEM ? 1 : 8], cc_r[SMEM ? 1 : 8][3];
+  float* sc = nullptr;
+  if constexpr (SMEM) {
+    __shared__ float pose_cache[32 * kBlock];
+    sc = pose_cache + threadIdx.x;
+  }
   float S[3] = {0.f, 0.f, 0.f}, SD = 0.f;
   float Ac[DIRT ? 8 : 1][3];
   if constexpr (DIRT) {
@@ -95,11 +103,16 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
         k = block_exit(r, ix, iy, iz, k, esh) - 1;
         continue;
       }
-      empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
+      if constexpr (SMEM)
+        empty = load_cell_smem<STORE>(P.g, ix, iy, iz, Y, l, sc);
+      else
+        empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs_r, cc_r);
     }
     if (empty) continue;
-    float w[8];
+    float w[8], cs[8];
     corner_weights(fx, fy, fz, w);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cs[c] = SMEM ? sc[(4 * c) * kBlock] : cs_r[SMEM ? 0 : c];
     float sig = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) sig = fmaf(w[c], cs[c], sig);
@@ -117,7 +130,10 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
       float V[8];
       float a = 0.f;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) { V[c] = cc[c][ch]; a = fmaf(w[c], V[c], a); }
+      for (int c = 0; c < 8; ++c) {
+        V[c] = SMEM ? sc[(4 * c + 1 + ch) * kBlock] : cc_r[SMEM ? 0 : c][ch];
+        a = fmaf(w[c], V[c], a);
+      }
       float dact;
       const float col = activate(a, P.o.color_act, dact);
       float gch[3];
@@ -197,7 +213,7 @@ __device__ __forceinline__ double warp_reduce_scatter(const float v[32], int lan
 // triangle of J^T W J (index hidx), v[21..26] = J^T W r, v[27] = r^T W r,
 // v[28] = 1 (count), with W = diag(1, 1, 1, lambda_d) (1/M is applied after the
 // reduction). rgb_t points at the ray's colour target, dz is its depth target.
-template <int STORE, bool DIRT = false>
+template <int STORE, bool DIRT = false, bool SMEM = false>
 __device__ __forceinline__ void pose_ray_values(const Common& P, const RayF& r,
                                                 const float* __restrict__ rgb_t, float dz,
                                                 float v[32]) {
@@ -214,7 +230,7 @@ __device__ __forceinline__ void pose_ray_values(const Common& P, const RayF& r,
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) A.G[ch][0] = A.G[ch][1] = A.G[ch][2] = 0.f;
   float C[3], D, T;
-  march_pose<STORE, DIRT>(P, r, Y, C, D, T, A);
+  march_pose<STORE, DIRT, SMEM>(P, r, Y, C, D, T, A);
   const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
   float res[4], J[4][6];
 #pragma unroll
