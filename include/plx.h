@@ -121,8 +121,8 @@ typedef struct {
 /* plx_render_opts.pose_flags. PLX_POSE_VIEW_DIR: the pose Jacobian also
  * differentiates the SH colour through the ray direction, dc/dd (a variant:
  * Sec. 5.3 holds the SH direction fixed). Honoured by plx_render_backward_pose,
- * plx_render_backward_pose_noalloc and plx_track_adam_step; the batched launch
- * rejects it. */
+ * plx_render_backward_pose_noalloc, plx_track_adam_step and the tracking items
+ * of plx_render_batch. */
 #define PLX_POSE_VIEW_DIR 1
 
 typedef struct {

@@ -639,8 +639,6 @@ extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cam
   dense.cam_id = nullptr;
   dense.pixel = nullptr;
   Common P;
-  if (opts && (opts->pose_flags & PLX_POSE_VIEW_DIR))
-    return fail(PLX_EINVAL, "%s: the view-direction variant is not in the batched launch", what);
   plx_status st = build_common(what, g, cams, &dense, opts, -1, PLX_FINE_BATCH, P);
   if (st != PLX_OK) return st;
   const CamTable base = P.ct;

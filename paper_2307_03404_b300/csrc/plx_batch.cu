@@ -39,7 +39,7 @@ __global__ void k_count_batch(const __grid_constant__ Common P, const float* __r
   if (lane == 0 && local) atomicAdd(M, local);
 }
 
-template <int STORE, int MINB>
+template <int STORE, int MINB, bool DIRT = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
         const float* __restrict__ depth_t, float* __restrict__ grad, double* __restrict__ map_loss,
@@ -74,7 +74,8 @@ k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
       float v[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = 0.f;
-      if (id.valid && depth_valid(dz)) pose_ray_values<STORE>(P, r, rgb_t + 3 * id.out, dz, v);
+      if (id.valid && depth_valid(dz))
+        pose_ray_values<STORE, DIRT>(P, r, rgb_t + 3 * id.out, dz, v);
       acc += warp_reduce_scatter(v, lane);
     } else if (id.valid && M > 0 && depth_valid(dz)) {
       float Y[9];
@@ -143,7 +144,14 @@ void launch_batch(int store, int minb, const Common& P, int n_track, const float
 #define PLX_BATCH(S, M_)                                                                      \
   k_batch<S, M_><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, grad, map_loss, Mmap, track_acc, \
                                            counter)
-    PLX_DISPATCH_SM(store, minb, PLX_BATCH);
+#define PLX_BATCH_DIR(S, M_)                                                                  \
+  k_batch<S, M_, true><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, grad, map_loss, Mmap,     \
+                                                 track_acc, counter)
+    if (P.o.dir_term)
+      PLX_DISPATCH_SM(store, minb, PLX_BATCH_DIR);
+    else
+      PLX_DISPATCH_SM(store, minb, PLX_BATCH);
+#undef PLX_BATCH_DIR
 #undef PLX_BATCH
   }
   const int fb = n_track > 0 ? (n_track + 127) / 128 : 1;

@@ -248,8 +248,8 @@ def test_backward_pose_matches_oracle(sphere):
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_backward_pose_view_direction_variant(sphere, storage):
     """PLX_POSE_VIEW_DIR (the SH colour also turns with the ray): the pose
-    system against the oracle's variant, on dense and list rays; it differs
-    from the paper's system, and the batched launch rejects the flag. Colour
+    system against the oracle's variant, on dense and list rays and in the
+    batched launch; it differs from the paper's system. Colour
     only (lambda_d = 0), identity activation and 4x SH, so the term is large
     enough to tell the two systems apart at the tolerance."""
     g0, cam, _, opts = sphere
@@ -280,9 +280,12 @@ def test_backward_pose_view_direction_variant(sphere, storage):
                                 rays=(np.zeros(700, np.int32), pix))
     assert norm_err(H2, ref2.H) <= TOL_GRAD
     assert norm_err(b2, ref2.b) <= TOL_GRAD
-    with pytest.raises(plx.PlxError, match="view-direction"):
-        plx.render_batch(case.grid, case.cams, [(0, plx.WORK_TRACK)], plx.opts_from_dict(ov),
-                         dev(rgb_t), dev(depth_t))
+    # the batched launch's tracking items honour the flag too
+    _, _, Hb, bb, lb = plx.render_batch(case.grid, case.cams, [(0, plx.WORK_TRACK)],
+                                        plx.opts_from_dict(ov), dev(rgb_t), dev(depth_t))
+    assert lb[0, 1].item() == ref.M
+    assert norm_err(Hb[0].cpu().numpy(), ref.H) <= TOL_GRAD
+    assert norm_err(bb[0].cpu().numpy(), ref.b) <= TOL_GRAD
 
 
 def test_pose_step_matches_oracle():
