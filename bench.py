@@ -61,14 +61,25 @@ def combine_rank_times(times_ms, units_per_rank):
     return sum(units_per_rank) / (t / 1e3), t
 
 
-def kernel_source_sha():
-    """Hash of the CUDA sources: a DRAM-traffic record taken with ncu applies
-    only to the kernels it was measured on."""
+# the sources each profiled kernel is built from
+KERNEL_SOURCES = {
+    "forward": ("plx_internal.cuh", "plx_march.cuh", "plx_render.cu"),
+    "backward_grid": ("plx_internal.cuh", "plx_march.cuh", "plx_render.cu"),
+}
+
+
+def kernel_source_sha(kernel=None):
+    """Hash of the CUDA sources (of one kernel's files, or of all): a
+    DRAM-traffic record taken with ncu applies only to the kernel it was
+    measured on."""
     import glob
     import hashlib
 
+    csrc = os.path.join(ROOT, "paper_2307_03404_b300", "csrc")
+    files = (sorted(glob.glob(os.path.join(csrc, "*.cu*"))) if kernel is None
+             else [os.path.join(csrc, f) for f in KERNEL_SOURCES[kernel]])
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2307_03404_b300", "csrc", "*.cu*"))):
+    for f in files:
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
@@ -81,7 +92,7 @@ def measured_traffic(kernel, workload, storage):
         return None
     for rec in json.load(open(p)):
         if (rec["kernel"] == kernel and rec["workload"] == workload
-                and rec["storage"] == storage and rec["source_sha"] == kernel_source_sha()):
+                and rec["storage"] == storage and rec["source_sha"] == kernel_source_sha(kernel)):
             return rec["dram_bytes_per_launch"]
     return None
 
