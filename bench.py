@@ -432,6 +432,7 @@ def run_ours(args):
                           "frame mapped into a dynamic 256^3 grid grown from depth, every frame "
                           "tracked (Adam, 200 iterations of 4096 random rays, one CUDA graph; again with "
                           "10 Levenberg-Marquardt iterations on whole frames)")
+        pl["scope"] = "one GPU (under torchrun every rank runs it; rank 0's numbers)"
         line["pipeline"] = pl
     if not args.no_cpu and rank == 0:
         line["cpu_baseline"] = cpu_baseline(sc, cams_np, rgb_np, depth_np, opts, args.cpu_seconds)
@@ -746,7 +747,8 @@ def run_large_bench(args, barrier):
                         "compulsory_bytes_per_launch": compulsory,
                         "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9},
            "loss": loss.cpu().tolist(), "launch_config": grid.get_config(),
-           "autotuned": tuned is not None, "steps": K}
+           "autotuned": tuned is not None, "steps": K,
+           "scope": "one GPU (under torchrun every rank runs it; rank 0's numbers)"}
     grid.close()
     return out
 
