@@ -84,17 +84,42 @@ def kernel_source_sha(kernel=None):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel, workload, storage):
-    """DRAM bytes per launch from profiles/traffic.json if it was taken on the
-    current kernel sources, else None."""
+def measured_profile(kernel, workload, storage):
+    """The ncu record of profiles/traffic.json (DRAM bytes and warp
+    instructions per launch) if it was taken on the current kernel sources,
+    else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     for rec in json.load(open(p)):
         if (rec["kernel"] == kernel and rec["workload"] == workload
                 and rec["storage"] == storage and rec["source_sha"] == kernel_source_sha(kernel)):
-            return rec["dram_bytes_per_launch"]
+            return rec
     return None
+
+
+def measured_traffic(kernel, workload, storage):
+    rec = measured_profile(kernel, workload, storage)
+    return rec["dram_bytes_per_launch"] if rec else None
+
+
+def issue_roofline(kernel, ms, storage, clocks):
+    """Instruction-issue utilisation of a kernel: warp instructions per launch
+    (ncu, profiles/traffic.json, valid for the current sources) over the live
+    launch time, against one warp instruction per clock per SM sub-partition
+    (4 per SM) at the SM clock sampled during the run."""
+    import torch
+
+    rec = measured_profile(kernel, "room256", storage)
+    if not rec or "warp_instructions_per_launch" not in rec:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2032.0
+    peak = sms * 4 * mhz * 1e6
+    achieved = rec["warp_instructions_per_launch"] / (ms / 1e3)
+    return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_launch": rec["warp_instructions_per_launch"],
+            "peak_basis": f"{sms} SMs x 4 sub-partitions x 1 warp instruction per clock x {mhz:.0f} MHz"}
 
 
 def peaks():
@@ -397,7 +422,8 @@ def run_ours(args):
                      "S_all_mean": s_all, "S_occ_mean": s_occ,
                      "touched_vertices": main["touched"],
                      "compulsory_bytes_per_launch": compulsory,
-                     "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9},
+                     "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9,
+                     "issue": issue_roofline(dom, dom_ms, args.storage, clocks)},
         "e2e": {"value": rays_job / (t_e2e / 1e3), "unit": "rays/s",
                 "h2d_bytes_per_step": main["h2d"], "d2h_bytes_per_step": main["d2h"],
                 "timing": "K steps as one region (first copy to last loss read); copies of "
