@@ -849,7 +849,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": dict(workload_config(sc, cams, "f64"), parallelism="host cores"),
+            "config": dict(workload_config(sc, cams, "f64"), parallelism="host cores",
+                           l2="not applicable (host run)"),
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step {n} seeded random rays of the workload"},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0,
@@ -876,7 +877,7 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--cpu-rays-per-step", type=int, default=512)
+    ap.add_argument("--cpu-rays-per-step", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3:
         log("[bench] warmup raised to 3")
