@@ -302,3 +302,32 @@ def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", de
     out["other_trackers"] = [tracked(c) for c in extra_track_cfgs]
     dg.close()
     return out
+
+
+def main(argv=None):
+    """Command line: run the pipeline on the seeded 256^3 room and print the
+    metrics as one JSON line (python -m paper_2307_03404_b300.pipeline)."""
+    import argparse
+    import json
+    import sys
+
+    from . import scenes
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--frames", type=int, default=300)
+    ap.add_argument("--span", type=float, default=0.3)
+    ap.add_argument("--map-every", type=int, default=10)
+    ap.add_argument("--map-steps", type=int, default=1000)
+    ap.add_argument("--tracker", choices=["adam", "lm"], default="adam")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16", "f32_bf16"])
+    a = ap.parse_args(argv)
+    R, occ, npr, seed = scenes.WORKLOADS["room256"]
+    sc = scenes.room_scene(R, occ, npr, seed)
+    out = run(sc, n_frames=a.frames, span=a.span, map_every=a.map_every, storage=a.storage,
+              map_cfg=MapConfig(iters=a.map_steps), track_cfg=TrackConfig(method=a.tracker),
+              log=lambda *m: print(*m, file=sys.stderr, flush=True))
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
