@@ -689,6 +689,23 @@ def run_batch_bench(args, barrier):
                         "launch_config": grid.get_config(),
                         "separate_calls": {"value": rows / (ms_s / 1e3), "ms": ms_s,
                                            "launches": 3 + 32}}
+        # the mapping optimiser on this grid (Sec. 5.4 RMSProp, one pass over
+        # all records, gradients and state): a plain streaming kernel, timed
+        # against the copy bandwidth
+        state = torch.zeros_like(grad)
+        n = grid.n_alloc
+        rec_r, rec_w = (112, 112) if storage == "f32" else (64, 64)
+        per_vertex = 112 + 112 + rec_r + 112 + 112 + rec_w  # grad, state r+w, record, zeroed grad
+
+        def rms():
+            plx.grid_rmsprop(grid, grad, state, 1e-3, lr_density=1e-2, zero_grad=True)
+
+        ms_r = timed(rms, max(3, args.steps), args.warmup)
+        hbm, peak_kind = peaks()
+        gbs = n * per_vertex / (ms_r / 1e3) / 1e9
+        out[storage]["rmsprop"] = {
+            "vertices": n, "ms": ms_r, "bytes_per_vertex": per_vertex, "achieved_gbs": gbs,
+            "peak_gbs": hbm, "frac": gbs / hbm, "peak_kind": f"{peak_kind} copy bandwidth"}
         grid.close()
     out["value"] = out["bf16"]["value"]
     return out

@@ -2,7 +2,8 @@
 // Adam on the pose for tracking with rays sampled at random from the frame.
 //
 // RMSProp is one elementwise pass over the allocated vertices (it cannot ride
-// on the adjoint's scatter: a gradient is final only once every ray is done):
+// on the adjoint's scatter: a gradient is final only once every ray is done),
+// streamed so that consecutive threads touch consecutive 16-byte chunks:
 // per value v <- alpha v + (1 - alpha) g^2, x <- x - lr g / (sqrt(v) + eps),
 // reading and writing the record in its storage format and, on request,
 // zeroing the gradient for the next step in the same pass.
@@ -82,23 +83,110 @@ __global__ void k_rmsprop(void* __restrict__ rec, float* __restrict__ grad,
   }
 }
 
+// Streaming forms: the same update with consecutive threads on consecutive
+// 16-byte chunks of the rows, so every warp load and store is contiguous.
+// FP32 records: thread j takes chunk q = j mod 7 of vertex j / 7 (4 values of
+// the record, the gradient and the state; the padding chunk 7 is skipped).
+__global__ void k_rmsprop_f32(float4* __restrict__ rec, float4* __restrict__ grad,
+                              float4* __restrict__ state, int64_t n, float lr_density, float lr_sh,
+                              float alpha, float eps, int zero_grad) {
+  const int64_t total = n * 7;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = j / 7;
+    const int q = (int)(j - v * 7);
+    const int64_t at = v * 8 + q;
+    const float4 g = grad[at];
+    float4 m = state[at];
+    float4 x = rec[at];
+    const float l0 = q == 0 ? lr_density : lr_sh;
+    x.x = rms_update(x.x, g.x, m.x, l0, alpha, eps);
+    x.y = rms_update(x.y, g.y, m.y, lr_sh, alpha, eps);
+    x.z = rms_update(x.z, g.z, m.z, lr_sh, alpha, eps);
+    x.w = rms_update(x.w, g.w, m.w, lr_sh, alpha, eps);
+    state[at] = m;
+    rec[at] = x;
+    if (zero_grad) grad[at] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// 16-bit records (BF16 or FP16, 2 values per word): thread j takes the
+// 16-byte record chunk q = j mod 4 of vertex j / 4 (values 8q .. 8q+7; for
+// q = 3 only 24..27 are values, 28..31 padding kept at zero) and the matching
+// two 16-byte chunks of the gradient and state rows.
+template <int STORE>
+__global__ void k_rmsprop_16(uint4* __restrict__ rec, float4* __restrict__ grad,
+                             float4* __restrict__ state, int64_t n, float lr_density, float lr_sh,
+                             float alpha, float eps, int zero_grad) {
+  const int64_t total = n * 4;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = j >> 2;
+    const int q = (int)(j & 3);
+    const int64_t ga = v * 8 + 2 * q;  // first of the two gradient / state chunks
+    const int nc = q < 3 ? 2 : 1;       // chunks holding values
+    uint4 w = rec[j];
+    uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h >= nc) break;
+      const float4 g = grad[ga + h];
+      float4 m = state[ga + h];
+      float x[4], gg[4] = {g.x, g.y, g.z, g.w}, mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const uint32_t word = ww[2 * h + e];
+        x[2 * e] = STORE == PLX_STORE_BF16 ? bf16_lo(word) : f16_lo(word);
+        x[2 * e + 1] = STORE == PLX_STORE_BF16 ? bf16_hi(word) : f16_hi(word);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float lr = (q == 0 && h == 0 && e == 0) ? lr_density : lr_sh;
+        x[e] = rms_update(x[e], gg[e], mm[e], lr, alpha, eps);
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if constexpr (STORE == PLX_STORE_BF16)
+          ww[2 * h + e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * e])) |
+                          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * e + 1])) << 16);
+        else
+          ww[2 * h + e] = (uint32_t)__half_as_ushort(__float2half_rn(x[2 * e])) |
+                          ((uint32_t)__half_as_ushort(__float2half_rn(x[2 * e + 1])) << 16);
+      }
+      state[ga + h] = make_float4(mm[0], mm[1], mm[2], mm[3]);
+      if (zero_grad) grad[ga + h] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    rec[j] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+  }
+}
+
 void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, float lr_density,
                     float lr_sh, float alpha, float eps, int zero_grad, int num_sms,
                     cudaStream_t s) {
   if (n <= 0) return;
   const int64_t want = (n + 255) / 256;
   const unsigned blocks = (unsigned)(want < 16 * num_sms ? want : 16 * num_sms);
+  const int64_t chunks = store == PLX_STORE_F32 ? n * 7 : n * 4;
+  const int64_t want_s = (chunks + 255) / 256;
+  const unsigned sblocks = (unsigned)(want_s < 16 * num_sms ? want_s : 16 * num_sms);
   switch (store) {
     case PLX_STORE_F32:
-      k_rmsprop<PLX_STORE_F32><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr_density, lr_sh, alpha, eps, zero_grad);
+      k_rmsprop_f32<<<sblocks, 256, 0, s>>>(reinterpret_cast<float4*>(rec),
+                                            reinterpret_cast<float4*>(grad),
+                                            reinterpret_cast<float4*>(state), n, lr_density, lr_sh,
+                                            alpha, eps, zero_grad);
       break;
     case PLX_STORE_BF16:
-      k_rmsprop<PLX_STORE_BF16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr_density, lr_sh, alpha, eps, zero_grad);
+      k_rmsprop_16<PLX_STORE_BF16><<<sblocks, 256, 0, s>>>(
+          reinterpret_cast<uint4*>(rec), reinterpret_cast<float4*>(grad),
+          reinterpret_cast<float4*>(state), n, lr_density, lr_sh, alpha, eps, zero_grad);
       break;
     case PLX_STORE_F16:
-      k_rmsprop<PLX_STORE_F16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr_density, lr_sh, alpha, eps, zero_grad);
+      k_rmsprop_16<PLX_STORE_F16><<<sblocks, 256, 0, s>>>(
+          reinterpret_cast<uint4*>(rec), reinterpret_cast<float4*>(grad),
+          reinterpret_cast<float4*>(state), n, lr_density, lr_sh, alpha, eps, zero_grad);
       break;
-    default:
+    default:  // FP32 density + BF16 SH: values straddle the chunks, one vertex per thread
       k_rmsprop<PLX_STORE_F32_BF16><<<blocks, 256, 0, s>>>(rec, grad, state, n, lr_density, lr_sh,
                                                            alpha, eps, zero_grad);
       break;
