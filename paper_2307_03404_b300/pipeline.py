@@ -79,6 +79,7 @@ class MapConfig:
     eps: float = 1e-8
     band: float = 2.0
     seed: int = 7
+    sort_rays: bool = True      # order each step's random rays for coherence
 
 
 @dataclasses.dataclass
@@ -99,6 +100,18 @@ class TrackConfig:
     lm_lambda: float = 1e-3
 
 
+def _morton2(x, y):
+    """Interleave the bits of two non-negative int64 tensors (< 2^16)."""
+    def spread(a):
+        a = a & 0xFFFF
+        a = (a | (a << 8)) & 0x00FF00FF
+        a = (a | (a << 4)) & 0x0F0F0F0F
+        a = (a | (a << 2)) & 0x33333333
+        a = (a | (a << 1)) & 0x55555555
+        return a
+    return spread(x) | (spread(y) << 1)
+
+
 def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: torch.Tensor,
                 opts, cfg: MapConfig, log=None):
     """Grow the grid from the keyframes' depth, then ``cfg.iters`` RMSProp
@@ -114,10 +127,20 @@ def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: 
     grad = torch.zeros(dg.n, plx.GRAD_STRIDE, device="cuda")
     losses = torch.zeros(cfg.iters, 2, dtype=torch.float64, device="cuda")
     fw = None
+    widths = torch.tensor([w for w, _ in cams.sizes], device="cuda")
     for it in range(cfg.iters):
         rows = torch.randint(0, total, (cfg.rays_per_step,), generator=gen, device="cuda")
-        cam_id = (torch.searchsorted(offs, rows, right=True) - 1).to(torch.int32)
-        pix = (rows - offs[cam_id.long()]).to(torch.int32)
+        cam_id = torch.searchsorted(offs, rows, right=True) - 1
+        pix = rows - offs[cam_id]
+        if cfg.sort_rays:
+            # the same random set, ordered by camera and then by the Z-order of
+            # the pixel, so the rays of a warp are neighbours in the image and
+            # share grid lines as dense tiles do
+            w = widths[cam_id]
+            key = (cam_id << 40) | _morton2(pix % w, pix // w)
+            order = torch.argsort(key)
+            rows, cam_id, pix = rows[order], cam_id[order], pix[order]
+        cam_id, pix = cam_id.to(torch.int32), pix.to(torch.int32)
         rays = (cam_id, pix)
         rgb_t, depth_t = rgb[rows], depth[rows]
         fw = plx.render_forward(dg.grid, cams, opts, rays=rays, out=fw)
