@@ -332,6 +332,9 @@ plx_status plx_grid_rmsprop(plx_grid *grid, float *grad, float *state,
  *   state  DEVICE double [20]: m[0..5], v[6..11], t at [12] (iterations done,
  *          also the generator counter), last xi at [13..18]; zeroed by the
  *          caller before the first iteration.
+ * Up to 8192 rays per iteration are drawn by a separate one-block kernel and
+ * launched in the Z-order of their pixels (the same set; only the order in
+ * which warps take them, and so the summation order, changes).
  * Asynchronous; graph-capturable (the counter lives on the device). */
 plx_status plx_track_adam_step(const plx_grid *grid, const plx_cameras *cams,
                                int32_t cam, const plx_render_opts *opts,

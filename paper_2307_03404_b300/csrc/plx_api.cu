@@ -31,6 +31,8 @@ void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, 
 void launch_pose_step_lm(const double* H, const double* b, const double* loss, double* state,
                          double lambda_init, double factor, double* pose, double* xi_out,
                          int32_t* status, cudaStream_t s);
+void launch_random_pixels_sorted(uint64_t seed, const double* iter, int n, int width, int height,
+                                 int32_t* out, cudaStream_t s);
 void launch_adam_pose(const double* JtWr, double* state, double* pose, double lr, double b1,
                       double b2, double eps, cudaStream_t s);
 void launch_batch(int store, int minb, const Common& P, int n_track, const float* rgb_t,
@@ -60,6 +62,7 @@ struct plx_grid {
   uint8_t* blk = nullptr;         // empty-space blocks (null: none)
   int nb[3] = {0, 0, 0};
   uint8_t* fblk = nullptr;        // second level, blocks of 2^kFineShift cells
+  int32_t* rand_pix = nullptr;    // Adam tracking: one iteration's pixels in image order
   int fnb[3] = {0, 0, 0};
   int rec_bytes = 0;
   char* ws = nullptr;
@@ -304,6 +307,7 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
     cudaFree(g->blk);
     cudaFree(g->fblk);
     cudaFree(g->ws);
+    cudaFree(g->rand_pix);
     delete g;
     return st;
   };
@@ -328,6 +332,7 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
   e = cudaMalloc(&g->links, (size_t)n_links * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&g->rec, (size_t)(desc->n_alloc > 0 ? desc->n_alloc : 1) * g->rec_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&g->ws, ws_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->rand_pix, kMaxSortedRays * sizeof(int32_t));
   if (e != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? PLX_ENOMEM : PLX_ECUDA,
                         "grid_create: allocation failed: %s", cudaGetErrorString(e)));
@@ -388,6 +393,7 @@ plx_status plx_grid_destroy(plx_grid* g) {
   cudaFree(g->blk);
   cudaFree(g->fblk);
   cudaFree(g->ws);
+  cudaFree(g->rand_pix);
   delete g;
   if (e != cudaSuccess) return fail(PLX_ECUDA, "grid_destroy: %s", cudaGetErrorString(e));
   return PLX_OK;
@@ -778,6 +784,11 @@ extern "C" plx_status plx_track_adam_step(const plx_grid* g, const plx_cameras* 
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
   double* partials = reinterpret_cast<double*>(g->ws + sizeof(Workspace));
   cudaStream_t s = (cudaStream_t)stream;
+  const plx_intrinsics& in = cams->intr[cam];
+  if (n_rays <= kMaxSortedRays && in.width <= 65535 && in.height <= 65535) {
+    launch_random_pixels_sorted(seed, state + 12, n_rays, in.width, in.height, g->rand_pix, s);
+    P.rl.pixel = g->rand_pix;
+  }
   launch_backward_pose(g->desc.storage, g->cfg.pose_blocks, P, rgb_target, depth_target, partials,
                        &ws->retire, JtWJ, JtWr, loss, g->pose_blocks, s);
   launch_adam_pose(JtWr, state, const_cast<double*>(cams->poses) + 12 * cam, lr, beta1, beta2, eps,

@@ -69,7 +69,8 @@ struct RayList {
   const int32_t* cam_id;          // list mode, may be null (single camera)
   const int32_t* pixel;           // list mode
   int32_t fixed_cam;              // >= 0: every ray belongs to this camera
-  int32_t random;                 // 1: rays are random pixels of fixed_cam (see below)
+  int32_t random;                 // 1: rays are random pixels of fixed_cam (see below;
+                                  // pixel, if set, holds them already drawn)
   uint64_t seed;                  // random mode: generator seed
   const double* iter;             // random mode: device iteration counter (an integer)
 };
@@ -95,6 +96,7 @@ constexpr int kDefaultPoseBlocks = 2;
 constexpr int kDefaultBatchBlocks = 1;
 constexpr int kDefaultFineSkip = PLX_FINE_ADJOINT | PLX_FINE_POSE | PLX_FINE_BATCH;
 constexpr int kFineShift = 1;         // second-level empty-space blocks: 2^1 cells per axis
+constexpr int kMaxSortedRays = 8192;  // Adam tracking: random rays put in image order up to this
 
 struct GridView {
   const int32_t* links;           // [rz][ry][rx]
@@ -185,7 +187,11 @@ __device__ __forceinline__ RayId ray_of(const Common& P, int64_t tile, int lane)
       const int c = P.rl.fixed_cam;
       const uint64_t t = (uint64_t)__ldg(P.rl.iter);
       const uint64_t npx = (uint64_t)P.ct.cam[c].width * P.ct.cam[c].height;
-      const int pix = (int)(splitmix64(P.rl.seed, t * (uint64_t)P.ct.n_rays + (uint64_t)i) % npx);
+      // the iteration's pixels, when already drawn and put in image order by
+      // k_random_pixels_sorted, else drawn here
+      const int pix = P.rl.pixel ? __ldg(P.rl.pixel + i)
+                                 : (int)(splitmix64(P.rl.seed, t * (uint64_t)P.ct.n_rays +
+                                                                   (uint64_t)i) % npx);
       r.cam = c;
       r.u = pix % P.ct.cam[c].width;
       r.v = pix / P.ct.cam[c].width;

@@ -193,6 +193,72 @@ void launch_rmsprop(int store, void* rec, float* grad, float* state, int64_t n, 
   }
 }
 
+// ------------------------------------------------ random rays, image order
+// The n pixels of Adam iteration t (pixel splitmix64(seed, t n + i) mod W H,
+// the same set as drawn inline) put in the Z-order of (u, v) by a bitonic sort
+// in shared memory, so that a warp's rays are image neighbours: they share grid
+// lines and take similar paths. One block; n <= kMaxSortedRays.
+__device__ __forceinline__ uint32_t spread_bits16(uint32_t a) {
+  a &= 0xFFFFu;
+  a = (a | (a << 8)) & 0x00FF00FFu;
+  a = (a | (a << 4)) & 0x0F0F0F0Fu;
+  a = (a | (a << 2)) & 0x33333333u;
+  a = (a | (a << 1)) & 0x55555555u;
+  return a;
+}
+
+__device__ __forceinline__ uint32_t compact_bits16(uint32_t a) {
+  a &= 0x55555555u;
+  a = (a | (a >> 1)) & 0x33333333u;
+  a = (a | (a >> 2)) & 0x0F0F0F0Fu;
+  a = (a | (a >> 4)) & 0x00FF00FFu;
+  a = (a | (a >> 8)) & 0x0000FFFFu;
+  return a;
+}
+
+__global__ void k_random_pixels_sorted(uint64_t seed, const double* __restrict__ iter, int n,
+                                       int width, int height, int32_t* __restrict__ out) {
+  __shared__ uint32_t keys[kMaxSortedRays];
+  const uint64_t t = (uint64_t)*iter;
+  const uint64_t npx = (uint64_t)width * height;
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    uint32_t key = 0xFFFFFFFFu;  // padding sorts last
+    if (i < n) {
+      const uint32_t pix = (uint32_t)(splitmix64(seed, t * (uint64_t)n + (uint64_t)i) % npx);
+      const uint32_t u = pix % (uint32_t)width, v = pix / (uint32_t)width;
+      key = spread_bits16(u) | (spread_bits16(v) << 1);
+    }
+    keys[i] = key;
+  }
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t a = keys[i], b = keys[ixj];
+          if ((a > b) == ((i & k) == 0)) {
+            keys[i] = b;
+            keys[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t key = keys[i];
+    out[i] = (int32_t)(compact_bits16(key >> 1) * (uint32_t)width + compact_bits16(key));
+  }
+}
+
+void launch_random_pixels_sorted(uint64_t seed, const double* iter, int n, int width, int height,
+                                 int32_t* out, cudaStream_t s) {
+  k_random_pixels_sorted<<<1, 1024, 0, s>>>(seed, iter, n, width, height, out);
+}
+
 // ---------------------------------------------------------------- Adam
 // state: m[0..5], v[6..11], t at [12] (iterations done), last step xi at
 // [13..18]. g = 2 JtWr is the loss gradient with respect to a left
