@@ -97,6 +97,7 @@ constexpr int kDefaultBatchBlocks = 1;
 constexpr int kDefaultFineSkip = PLX_FINE_ADJOINT | PLX_FINE_POSE | PLX_FINE_BATCH;
 constexpr int kFineShift = 1;         // second-level empty-space blocks: 2^1 cells per axis
 constexpr int kMaxSortedRays = 8192;  // Adam tracking: random rays put in image order up to this
+constexpr int64_t kSegRays = 16384;   // pose Jacobian: a warp per ray up to this many rays
 
 struct GridView {
   const int32_t* links;           // [rz][ry][rx]

@@ -26,7 +26,10 @@
 
 namespace plx {
 
-template <int STORE, int MINB, bool DIRT = false>
+// SEGK: one ray per warp, its samples split over the lanes
+// (pose_ray_values_seg), for ray counts too small to fill the GPU one ray per
+// thread; otherwise one ray per thread, a warp per 32 rays.
+template <int STORE, int MINB, bool DIRT = false, bool SEGK = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
                 const float* __restrict__ depth_t, double* __restrict__ partials,
@@ -37,7 +40,25 @@ k_backward_pose(const __grid_constant__ Common P, const float* __restrict__ rgb_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc = 0.0;
   const int64_t warps_total = (int64_t)gridDim.x * kWarpsPerBlock;
-  for (int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + warp; tile < P.ct.n_tiles;
+  if constexpr (SEGK) {
+    const int64_t n_slots = P.ct.n_tiles * 32;  // ray slots (some invalid in dense mode)
+    for (int64_t ray = (int64_t)blockIdx.x * kWarpsPerBlock + warp; ray < n_slots;
+         ray += warps_total) {
+      const RayId id = ray_of(P, ray >> 5, (int)(ray & 31));
+      RayF r;
+      setup_ray(P, id, r, lane);
+      const float dz = id.valid ? __ldg(depth_t + id.out) : 0.f;
+      if (id.valid && depth_valid(dz)) {  // warp-uniform: every lane has the same ray
+        float v[32];
+        pose_ray_values_seg<STORE>(P, r, rgb_t + 3 * id.out, dz, lane, v);
+        float mine = 0.f;
+#pragma unroll
+        for (int i = 0; i < 29; ++i) mine = i == lane ? v[i] : mine;
+        acc += (double)mine;
+      }
+    }
+  }
+  for (int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + warp; !SEGK && tile < P.ct.n_tiles;
        tile += warps_total) {
     float v[32];
 #pragma unroll
@@ -224,10 +245,21 @@ void launch_backward_pose(int store, int minb, const Common& P, const float* rgb
 #define PLX_POSE_DIR(S, M)                                                             \
   k_backward_pose<S, M, true><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, partials,   \
                                                         retire, JtWJ, JtWr, loss)
-  if (P.o.dir_term)
+#define PLX_POSE_SEG(S, M)                                                                    \
+  k_backward_pose<S, M, false, true><<<seg_blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, partials, \
+                                                                   retire, JtWJ, JtWr, loss)
+  // few rays: a warp per ray (needs stop_T = 0; the paper's Jacobian only)
+  const bool seg = P.ct.n_tiles * 32 <= kSegRays && !(P.o.stop_T > 0.f) && !P.o.dir_term;
+  int64_t seg_want = (P.ct.n_tiles * 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (seg_want < 1) seg_want = 1;
+  const unsigned seg_blocks = (unsigned)(seg_want < max_blocks ? seg_want : max_blocks);
+  if (seg)
+    PLX_DISPATCH_SM(store, minb, PLX_POSE_SEG);
+  else if (P.o.dir_term)
     PLX_DISPATCH_SM(store, minb, PLX_POSE_DIR);
   else
     PLX_DISPATCH_SM(store, minb, PLX_POSE);
+#undef PLX_POSE_SEG
 #undef PLX_POSE_DIR
 #undef PLX_POSE
 }

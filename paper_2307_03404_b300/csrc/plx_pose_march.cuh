@@ -63,9 +63,14 @@ __device__ __forceinline__ void dir_flush(const GridView& g, const int32_t l[8],
 // SMEM: the cell's corner cache lives in shared memory (slot s of this
 // thread at sc[s * kBlock], as in the adjoint), so registers hold the corner
 // values only while a sample uses them.
-template <int STORE, bool DIRT = false, bool SMEM = false>
+// SEG: march only samples [k0, k1) of the ray as if they were the whole ray
+// (transmittance from 1, colour and depth sums from 0, no background, no early
+// stop): the segment's local quantities, combined across segments by
+// pose_ray_values_seg.
+template <int STORE, bool DIRT = false, bool SMEM = false, bool SEG = false>
 __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const float Y[9],
-                                           float C[3], float& D, float& T, PoseAcc& A) {
+                                           float C[3], float& D, float& T, PoseAcc& A,
+                                           int k0 = 0, int k1 = 0) {
   const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
   const float ihx = (float)P.g.inv_h[0], ihy = (float)P.g.inv_h[1], ihz = (float)P.g.inv_h[2];
   int cx = -1, cy = -1, cz = -1;
@@ -85,7 +90,8 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
   }
   T = 1.f;
   const float dt = r.dt;
-  for (int k = 0; k < r.n; ++k) {
+  const int k_end = SEG ? k1 : r.n;
+  for (int k = SEG ? k0 : 0; k < k_end; ++k) {
     const float kf = (float)k;
     int ix, iy, iz;
     float fx, fy, fz;
@@ -165,13 +171,13 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
       A.Qd[a] = fmaf(t, q, A.Qd[a]);
     }
     T = Tn;
-    if (T < P.o.stop_T) break;
+    if (!SEG && T < P.o.stop_T) break;
   }
   if constexpr (DIRT) {
     if (!empty) dir_flush<STORE>(P.g, l, Ac, r.dir, A.G);
   }
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], S[ch]);
+  for (int ch = 0; ch < 3; ++ch) C[ch] = SEG ? S[ch] : fmaf(T, P.o.bg[ch], S[ch]);
   D = SD;
 }
 
@@ -209,28 +215,14 @@ __device__ __forceinline__ double warp_reduce_scatter(const float v[32], int lan
   return (double)a[0].h + (double)a[0].l;
 }
 
-// One valid ray's contribution to the Gauss-Newton system: v[0..20] = the upper
-// triangle of J^T W J (index hidx), v[21..26] = J^T W r, v[27] = r^T W r,
-// v[28] = 1 (count), with W = diag(1, 1, 1, lambda_d) (1/M is applied after the
-// reduction). rgb_t points at the ray's colour target, dz is its depth target.
-template <int STORE, bool DIRT = false, bool SMEM = false>
-__device__ __forceinline__ void pose_ray_values(const Common& P, const RayF& r,
-                                                const float* __restrict__ rgb_t, float dz,
-                                                float v[32]) {
+// The ray's 29 values from its colour C, depth D and accumulators (see
+// pose_ray_values).
+template <bool DIRT>
+__device__ __forceinline__ void pose_values_from(const Common& P, const RayF& r,
+                                                 const float* __restrict__ rgb_t, float dz,
+                                                 const float C[3], float D, const PoseAcc& A,
+                                                 float v[32]) {
   const float lam = P.o.lambda_d;
-  float Y[9];
-  sh_basis(r.dir, Y);
-  PoseAcc A;
-#pragma unroll
-  for (int x = 0; x < 4; ++x)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) A.Po[x][a] = A.Pd[x][a] = 0.f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) A.Qo[a] = A.Qd[a] = 0.f;
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) A.G[ch][0] = A.G[ch][1] = A.G[ch][2] = 0.f;
-  float C[3], D, T;
-  march_pose<STORE, DIRT, SMEM>(P, r, Y, C, D, T, A);
   const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
   float res[4], J[4][6];
 #pragma unroll
@@ -269,6 +261,117 @@ __device__ __forceinline__ void pose_ray_values(const Common& P, const RayF& r,
   }
   v[27] = res[0] * res[0] + res[1] * res[1] + res[2] * res[2] + lam * res[3] * res[3];
   v[28] = 1.f;
+}
+
+// One valid ray's contribution to the Gauss-Newton system: v[0..20] = the upper
+// triangle of J^T W J (index hidx), v[21..26] = J^T W r, v[27] = r^T W r,
+// v[28] = 1 (count), with W = diag(1, 1, 1, lambda_d) (1/M is applied after the
+// reduction). rgb_t points at the ray's colour target, dz is its depth target.
+template <int STORE, bool DIRT = false, bool SMEM = false>
+__device__ __forceinline__ void pose_ray_values(const Common& P, const RayF& r,
+                                                const float* __restrict__ rgb_t, float dz,
+                                                float v[32]) {
+  float Y[9];
+  sh_basis(r.dir, Y);
+  PoseAcc A;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) A.Po[x][a] = A.Pd[x][a] = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) A.Qo[a] = A.Qd[a] = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) A.G[ch][0] = A.G[ch][1] = A.G[ch][2] = 0.f;
+  float C[3], D, T;
+  march_pose<STORE, DIRT, SMEM>(P, r, Y, C, D, T, A);
+  pose_values_from<DIRT>(P, r, rgb_t, dz, C, D, A, v);
+}
+
+// Warp-per-ray form of pose_ray_values, for few rays (tracking on a random
+// subset of a frame): the 32 lanes of the warp march consecutive segments of
+// the same ray, each from transmittance 1 and zero sums. A segment's true
+// transmittance at entry T0 and colour/depth sums S0, SD0 follow from an
+// exclusive scan over the lanes of (T_seg, S_seg) under
+// (T_a, S_a) o (T_b, S_b) = (T_a T_b, S_a + T_a S_b); every per-sample term of
+// the single-pass Jacobian is then T0 times its local value plus S0 (SD0 for
+// depth) times the local Q = sum delta grad sigma, so the ray's sums are
+// sum_lanes (T0 P_loc + S0 Q_loc). The warp then holds the whole ray's values
+// in every lane. Needs stop_T = 0 (a lane cannot stop on the global T).
+// Must be called by all 32 lanes with the same ray.
+template <int STORE>
+__device__ __forceinline__ void pose_ray_values_seg(const Common& P, const RayF& r,
+                                                    const float* __restrict__ rgb_t, float dz,
+                                                    int lane, float v[32]) {
+  float Y[9];
+  sh_basis(r.dir, Y);
+  PoseAcc A;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) A.Po[x][a] = A.Pd[x][a] = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) A.Qo[a] = A.Qd[a] = 0.f;
+  const int k0 = (int)(((int64_t)r.n * lane) >> 5), k1 = (int)(((int64_t)r.n * (lane + 1)) >> 5);
+  float S[3], SD, T;
+  march_pose<STORE, false, true, true>(P, r, Y, S, SD, T, A, k0, k1);
+  // inclusive scan of (T, S[3], SD) over lanes, then shift to exclusive
+  float iT = T, iS0 = S[0], iS1 = S[1], iS2 = S[2], iSD = SD;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float pT = __shfl_up_sync(0xffffffffu, iT, off);
+    const float p0 = __shfl_up_sync(0xffffffffu, iS0, off);
+    const float p1 = __shfl_up_sync(0xffffffffu, iS1, off);
+    const float p2 = __shfl_up_sync(0xffffffffu, iS2, off);
+    const float pD = __shfl_up_sync(0xffffffffu, iSD, off);
+    if (lane >= off) {  // (earlier prefix) o (this lane's inclusive part)
+      iS0 = fmaf(pT, iS0, p0);
+      iS1 = fmaf(pT, iS1, p1);
+      iS2 = fmaf(pT, iS2, p2);
+      iSD = fmaf(pT, iSD, pD);
+      iT *= pT;
+    }
+  }
+  float T0 = __shfl_up_sync(0xffffffffu, iT, 1);
+  float S00 = __shfl_up_sync(0xffffffffu, iS0, 1), S01 = __shfl_up_sync(0xffffffffu, iS1, 1);
+  float S02 = __shfl_up_sync(0xffffffffu, iS2, 1), SD0 = __shfl_up_sync(0xffffffffu, iSD, 1);
+  if (lane == 0) T0 = 1.f, S00 = S01 = S02 = SD0 = 0.f;
+  const float Tn = __shfl_sync(0xffffffffu, iT, 31);
+  float C[3] = {__shfl_sync(0xffffffffu, iS0, 31), __shfl_sync(0xffffffffu, iS1, 31),
+                __shfl_sync(0xffffffffu, iS2, 31)};
+  const float D = __shfl_sync(0xffffffffu, iSD, 31);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(Tn, P.o.bg[ch], C[ch]);
+  // this lane's share of the ray's sums, then the warp sum in every lane
+  const float S0[4] = {S00, S01, S02, SD0};
+  PoseAcc R;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R.Po[x][a] = fmaf(T0, A.Po[x][a], S0[x] * A.Qo[a]);
+      R.Pd[x][a] = fmaf(T0, A.Pd[x][a], S0[x] * A.Qd[a]);
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {  // Q = sum delta grad sigma does not depend on T
+    R.Qo[a] = A.Qo[a];
+    R.Qd[a] = A.Qd[a];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        R.Po[x][a] += __shfl_xor_sync(0xffffffffu, R.Po[x][a], off);
+        R.Pd[x][a] += __shfl_xor_sync(0xffffffffu, R.Pd[x][a], off);
+      }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R.Qo[a] += __shfl_xor_sync(0xffffffffu, R.Qo[a], off);
+      R.Qd[a] += __shfl_xor_sync(0xffffffffu, R.Qd[a], off);
+    }
+  }
+  pose_values_from<false>(P, r, rgb_t, dz, C, D, R, v);
 }
 
 }  // namespace plx

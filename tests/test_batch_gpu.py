@@ -58,8 +58,10 @@ def test_batch_matches_separate_calls_and_oracle():
         sl = slice(offs[i], offs[i + 1])
         H2, b2, l3 = plx.render_backward_pose(grid, cams, c, o, dev(rgb_t[sl]), dev(depth_t[sl]))
         assert tloss[s, 1].item() == l3[1].item()
-        assert norm_err(H[s].cpu().numpy(), H2.cpu().numpy()) <= 1e-9
-        assert norm_err(b[s].cpu().numpy(), b2.cpu().numpy()) <= 1e-9
+        # small frames take the warp-per-ray pose kernel in the separate call:
+        # the same per-ray terms, FP32 sums in another order
+        assert norm_err(H[s].cpu().numpy(), H2.cpu().numpy()) <= 1e-5
+        assert norm_err(b[s].cpu().numpy(), b2.cpu().numpy()) <= 1e-5
         pr = oracle.pose_jacobian(g, [cams_np[c]], opts_d, rgb_t[sl], depth_t[sl])
         assert norm_err(H[s].cpu().numpy(), pr.H) <= 1e-4
         assert norm_err(b[s].cpu().numpy(), pr.b) <= 1e-4
