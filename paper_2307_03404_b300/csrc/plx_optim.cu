@@ -268,6 +268,18 @@ __global__ void k_adam_pose(const double* __restrict__ JtWr, double* __restrict_
                             double eps) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double t = state[12] + 1.0;
+  // bias corrections 1 - b^t; t is an integer, so b^t by repeated squaring
+  // (a few multiplications instead of a transcendental pow per component)
+  double p1 = 1.0, p2 = 1.0, s1 = b1, s2 = b2;
+  for (uint64_t e = (uint64_t)t; e; e >>= 1) {
+    if (e & 1) {
+      p1 *= s1;
+      p2 *= s2;
+    }
+    s1 *= s1;
+    s2 *= s2;
+  }
+  const double c1 = 1.0 / (1.0 - p1), c2 = 1.0 / (1.0 - p2);
   double xi[6];
   for (int j = 0; j < 6; ++j) {
     const double g = 2.0 * JtWr[j];
@@ -275,9 +287,7 @@ __global__ void k_adam_pose(const double* __restrict__ JtWr, double* __restrict_
     const double v = b2 * state[6 + j] + (1.0 - b2) * g * g;
     state[j] = m;
     state[6 + j] = v;
-    const double mh = m / (1.0 - pow(b1, t));
-    const double vh = v / (1.0 - pow(b2, t));
-    xi[j] = -lr * mh / (sqrt(vh) + eps);
+    xi[j] = -lr * (m * c1) / (sqrt(v * c2) + eps);
   }
   state[12] = t;
   for (int j = 0; j < 6; ++j) state[13 + j] = xi[j];
