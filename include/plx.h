@@ -65,7 +65,7 @@ typedef enum {
   PLX_ECUDA = 3,         /* a CUDA runtime call failed */
   PLX_EDEVICE_CHECK = 4, /* a device-side check failed (see plx_grid_check) */
   PLX_ETIMEOUT = 5,      /* a bounded device wait gave up */
-  PLX_EUNSUPPORTED = 6   /* option not supported by this build */
+  PLX_EUNSUPPORTED = 6   /* option not supported by this library */
 } plx_status;
 
 /* Storage of the 28 values of a vertex inside the library. Every mode
