@@ -22,9 +22,9 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
     const float kf = (float)k;
     int ix, iy, iz;
     float fx, fy, fz;
-    sample_axis(r.bh[0], r.bl[0], r.sh[0], r.sl[0], kf, rm2x, ix, fx);
-    sample_axis(r.bh[1], r.bl[1], r.sh[1], r.sl[1], kf, rm2y, iy, fy);
-    sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
+    sample_axis(r.B[0], r.S[0], k, rm2x, ix, fx);
+    sample_axis(r.B[1], r.S[1], k, rm2y, iy, fy);
+    sample_axis(r.B[2], r.S[2], k, rm2z, iz, fz);
     if (ix != cx || iy != cy || iz != cz) {
       cx = ix; cy = iy; cz = iz;
       const int esh = empty_block_shift(P.g, ix, iy, iz);
@@ -141,9 +141,9 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
     const float kf = (float)k;
     int ix, iy, iz;
     float fx, fy, fz;
-    sample_axis(r.bh[0], r.bl[0], r.sh[0], r.sl[0], kf, rm2x, ix, fx);
-    sample_axis(r.bh[1], r.bl[1], r.sh[1], r.sl[1], kf, rm2y, iy, fy);
-    sample_axis(r.bh[2], r.bl[2], r.sh[2], r.sl[2], kf, rm2z, iz, fz);
+    sample_axis(r.B[0], r.S[0], k, rm2x, ix, fx);
+    sample_axis(r.B[1], r.S[1], k, rm2y, iy, fy);
+    sample_axis(r.B[2], r.S[2], k, rm2z, iz, fz);
     if (ix != cx || iy != cy || iz != cz) {
       const int esh = empty_block_shift(P.g, ix, iy, iz);
       const bool skip = esh >= 0;
