@@ -210,18 +210,39 @@ def workload_config(sc, cams, storage):
 
 
 # ------------------------------------------------------------------- ours
-def bytes_model(counts, storage, valid):
+def cache_note(res, n_rays):
+    """How the mapping step used the sample cache, for the JSON line."""
+    if not res["cache"]:
+        return "off: the adjoint re-marches every ray"
+    k, cap = res["kept"], res["cache"]["cap"]
+    return (f"{cap} compositing samples per ray kept by the forward for the adjoint "
+            f"({res['cache']['bytes'] / 1e9:.2f} GB, sized untimed by a probe forward); "
+            f"mean {k.mean():.1f}, max {int(k.max())} per ray; "
+            f"{int((k > cap).sum())} of {n_rays} rays re-marched")
+
+
+def bytes_model(counts, storage, valid, kept=None, cap=0):
     """Algorithmic bytes of the forward and the adjoint launch over these rays
     (no reuse: every marched sample reads its 8 links, every sample with an
     allocated corner gathers 8 records, the adjoint adds a read-modify-write of
-    8 FP32 gradient rows per such sample; per-ray I/O on top)."""
+    8 FP32 gradient rows per such sample; per-ray I/O on top). With a sample
+    cache (``kept`` = compositing samples per ray, ``cap``) the forward also
+    writes 20 B per kept sample and 4 B per ray, and the adjoint of a ray that
+    fits reads them back and, per kept sample, its 8 links and the gradient
+    rows' read-modify-write; a ray that overflows is re-marched as without."""
     n_rays = counts.shape[0]
     rec = 896.0 if storage == "f32" else 448.0
     s_all = counts[:, 0].astype(np.float64)
     s_occ = counts[:, 1].astype(np.float64)
     fwd = (s_all * 32 + s_occ * rec).sum() + 20.0 * n_rays
-    bwd = (s_all[valid] * 32 + s_occ[valid] * (rec + 1792.0)).sum() + 32.0 * valid.sum() \
+    full = valid if kept is None else valid & (kept > cap)
+    bwd = (s_all[full] * 32 + s_occ[full] * (rec + 1792.0)).sum() + 32.0 * valid.sum() \
         + 4.0 * n_rays
+    if kept is not None:
+        k = kept.astype(np.float64)
+        fwd += 20.0 * np.minimum(k, cap).sum() + 4.0 * n_rays
+        fit = valid & (kept <= cap)
+        bwd += (k[fit] * (20.0 + 32.0 + 1792.0)).sum() + 4.0 * n_rays
     return fwd, bwd, float(s_all.mean()), float(s_occ.mean())
 
 
@@ -246,7 +267,7 @@ def run_ours(args):
     sc, cams_np, rgb_np, depth_np, opts = mapping_workload(world, rank)
     n_rays = rgb_np.shape[0]
     cams = plx.CameraSet(cams_np)
-    o = plx.opts_from_dict(opts)
+    o_plain = plx.opts_from_dict(opts)
     rgb_t = torch.from_numpy(rgb_np).cuda()
     depth_t = torch.from_numpy(depth_np).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -256,6 +277,16 @@ def run_ours(args):
 
     def measure(storage, K, W, with_e2e):
         grid = plx.Grid.from_scene(sc.grid, storage)
+        # sample cache: forward keeps each ray's compositing samples for the
+        # adjoint; sized (untimed) by a probe forward so that no ray overflows
+        scache = None
+        o = o_plain
+        if args.sample_cache != "off":
+            if args.sample_cache == "fit":
+                scache = plx.SampleCache.sized_for(grid, cams, o_plain)
+            else:
+                scache = plx.SampleCache(n_rays, int(args.sample_cache))
+            o = scache.opts(o_plain)
         tuned = None
         if not args.no_tune:
             from paper_2307_03404_b300 import autotune
@@ -356,10 +387,14 @@ def run_ours(args):
             res["d2h"] = loss_h.numel() * 8
         # exact sample counts for the byte model, and the vertices the step
         # touched for the compulsory-traffic bound (untimed)
-        cnt = plx.render_forward(grid, cams, o, counts=True)["counts"].cpu().numpy()
+        res["kept"] = scache.counts().cpu().numpy().copy() if scache is not None else None
+        res["cache"] = ({"cap": scache.cap, "bytes": plx.sample_cache_bytes(n_rays, scache.cap)}
+                        if scache is not None else None)
+        cnt = plx.render_forward(grid, cams, o_plain, counts=True)["counts"].cpu().numpy()
         res["counts"] = cnt
         res["touched"] = int((grad[:, :28] != 0).any(1).sum())
         grid.close()
+        del scache
         return res
 
     K, W = args.steps, args.warmup
@@ -385,13 +420,16 @@ def run_ours(args):
     valid = np.isfinite(depth_np) & (depth_np > 0)
     hbm, peak_kind = peaks()
 
-    fwd_b, bwd_b, s_all, s_occ = bytes_model(main["counts"], args.storage, valid)
+    cap_main = main["cache"]["cap"] if main["cache"] else 0
+    fwd_b, bwd_b, s_all, s_occ = bytes_model(main["counts"], args.storage, valid, main["kept"],
+                                             cap_main)
     fwd_ms, bwd_ms = statistics.mean(main["fwd_ms"]), statistics.mean(main["bwd_ms"])
     dom = "backward_grid" if bwd_ms >= fwd_ms else "forward"
     dom_b, dom_ms = (bwd_b, bwd_ms) if dom == "backward_grid" else (fwd_b, fwd_ms)
     achieved = dom_b / (dom_ms / 1e3) / 1e9
     step_roof = (fwd_b + bwd_b) / (hbm * 1e9) * 1e3   # ms per step at the HBM roof
-    fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage, valid)
+    fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage, valid, other["kept"],
+                                   other["cache"]["cap"] if other["cache"] else 0)
 
     # compulsory traffic of the adjoint: every touched vertex's record read
     # once, its FP32 gradient row read and written once, its link once
@@ -405,15 +443,20 @@ def run_ours(args):
         "warmup": W, "ms_per_step": t_main / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(sc, cams_np, args.storage),
-                       parallelism=f"replicated grid, keyframes sharded over {world} rank(s)"),
+                       parallelism=f"replicated grid, keyframes sharded over {world} rank(s)",
+                       sample_cache=cache_note(main, n_rays)),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": measured_traffic(dom, "room256", args.storage),
                      "model": "no-reuse byte model: 32 B of links per marched sample and pass, "
                               "896 B (f32) / 448 B (16-bit) per gathered sample with an "
-                              "allocated corner, 1792 B of FP32 gradient RMW per such sample "
-                              "in the adjoint, 32-36 B of per-ray I/O; frac > 1 = beating "
-                              "the no-reuse bound through L1/L2 reuse",
+                              "allocated corner, 32-36 B of per-ray I/O; with the sample "
+                              "cache the forward writes 20 B per compositing sample and the "
+                              "adjoint reads them back with 32 B of links and 1792 B of FP32 "
+                              "gradient RMW per such sample (rays that overflow the cache: "
+                              "32 B per marched sample, 896/448 + 1792 B per sample with an "
+                              "allocated corner); frac > 1 = beating the no-reuse bound "
+                              "through L1/L2 reuse",
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_per_launch": dom_b, "ms_per_launch": dom_ms,
                      "step_frac": step_roof / (t_main / K),
@@ -429,7 +472,7 @@ def run_ours(args):
                 "timing": "K steps as one region (first copy to last loss read); copies of "
                           "step i+1 overlap step i on a second stream; L2 flushed per step "
                           "inside the region"},
-        "gpu_launches": K * 3,
+        "gpu_launches": K * (4 if main["cache"] else 3),
         "clocks": clocks,
         other_storage: {"value": rays_job / (t_other / 1e3), "unit": "rays/s",
                         "ms_per_step": t_other / K,
@@ -739,6 +782,12 @@ def run_large_bench(args, barrier):
     grid = plx.Grid.from_scene(sc.grid, storage)
     n_alloc = grid.n_alloc
     del sc
+    o_plain = o
+    scache = None
+    if args.sample_cache != "off":
+        scache = (plx.SampleCache.sized_for(grid, cams, o_plain) if args.sample_cache == "fit"
+                  else plx.SampleCache(n_rays, int(args.sample_cache)))
+        o = scache.opts(o_plain)
     tuned = None
     if not args.no_tune:
         from paper_2307_03404_b300 import autotune
@@ -771,10 +820,15 @@ def run_large_bench(args, barrier):
     fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in E)
     bwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in E)
     step_ms = fwd_ms + bwd_ms
-    counts = plx.render_forward(grid, cams, o, counts=True)["counts"].cpu().numpy()
+    kept = scache.counts().cpu().numpy().copy() if scache is not None else None
+    cache_res = ({"cap": scache.cap, "bytes": plx.sample_cache_bytes(n_rays, scache.cap)}
+                 if scache is not None else None)
+    del scache
+    counts = plx.render_forward(grid, cams, o_plain, counts=True)["counts"].cpu().numpy()
     d = depth_t.cpu().numpy()
     valid = np.isfinite(d) & (d > 0)
-    fwd_b, bwd_b, s_all, s_occ = bytes_model(counts, storage, valid)
+    fwd_b, bwd_b, s_all, s_occ = bytes_model(counts, storage, valid, kept,
+                                             cache_res["cap"] if cache_res else 0)
     hbm, peak_kind = peaks()
     achieved = bwd_b / (bwd_ms / 1e3) / 1e9
     touched = int((grad[:, :28] != 0).any(1).sum())
@@ -793,6 +847,7 @@ def run_large_bench(args, barrier):
                         "compulsory_bytes_per_launch": compulsory,
                         "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9},
            "loss": loss.cpu().tolist(), "launch_config": grid.get_config(),
+           "sample_cache": cache_note({"cache": cache_res, "kept": kept}, n_rays),
            "autotuned": tuned is not None, "steps": K,
            "scope": "one GPU (under torchrun every rank runs it; rank 0's numbers)"}
     grid.close()
@@ -896,6 +951,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
+    ap.add_argument("--sample-cache", default="fit",
+                    help='"fit" (sized so no ray overflows), "off", or samples per ray')
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-rays-per-step", type=int, default=4096)
     args = ap.parse_args()

@@ -135,7 +135,32 @@ typedef struct {
   int32_t color_act;   /* plx_color_act */
   int32_t depth_is_z;  /* 1: depth targets are z-depths; 0: ray distances */
   int32_t pose_flags;  /* 0, or PLX_POSE_VIEW_DIR (pose calls only) */
+  void *sample_cache;  /* DEVICE, 16-byte aligned, or NULL: the sample cache
+                          of plx_render_forward / plx_render_backward_grid
+                          (ignored by every other call) */
+  int32_t sample_cap;  /* K: samples kept per ray in sample_cache, >= 0 */
+  int64_t sample_rays; /* n: rays the cache was sized for (its row stride),
+                          >= the call's n_rays */
 } plx_render_opts;
+
+/* Sample cache (Sec. 5.2: what the adjoint of Eq. 8-10 needs per sample).
+ * With opts->sample_cache set and opts->sample_cap = K > 0, plx_render_forward
+ * keeps, for each ray, its first K samples with sigma > 0 (the ones that
+ * composite): the sample index k, the density before the ReLU and the
+ * activated colour. plx_render_backward_grid then visits only those samples
+ * (no empty-space march, no record gathers, no SH projection; it still loads
+ * the cells' links to scatter into the corners) and re-marches in full only
+ * the rays that had more than K. Layout, n = opts->sample_rays:
+ *   float [K][n][4]  (sigma, c_r, c_g, c_b) of kept sample j of ray r at [j][r]
+ *   int32 [K][n]     its sample index k
+ *   int32 [n]        the ray's number of samples with sigma > 0 (may exceed K)
+ * in plx_sample_cache_bytes(n, K) bytes, owned by the caller; a call over more
+ * than n rays fails with PLX_EINVAL. The adjoint
+ * call must name the same cache and K, grid contents, cameras, rays and opts
+ * as the forward that filled it (nothing checks this); without a cache it
+ * re-marches every ray. Both ways give the same gradients up to the order of
+ * floating-point sums. */
+int64_t plx_sample_cache_bytes(int64_t n_rays, int32_t cap); /* -1 if either < 0 */
 
 const char *plx_last_error(void);
 const char *plx_version(void);
@@ -179,7 +204,9 @@ plx_status plx_grid_destroy(plx_grid *grid);
  *   state_out DEVICE float [n_rays]     final transmittance T_{N+1}, or NULL
  *   counts_out DEVICE int32 [n_rays][2] samples marched and samples with an
  *             allocated corner, or NULL (counting costs a little time)
- * Output row r is ray r (see plx_rays). Errors: PLX_EINVAL, PLX_ECUDA. */
+ * With opts->sample_cache it also fills the sample cache (see above).
+ * Output row r is ray r (see plx_rays). Errors: PLX_EINVAL (also a sample
+ * cache that is not 16-byte aligned), PLX_ECUDA. */
 plx_status plx_render_forward(const plx_grid *grid, const plx_cameras *cams,
                               const plx_rays *rays, const plx_render_opts *opts,
                               float *rgb_out, float *depth_out, float *state_out,
@@ -187,9 +214,9 @@ plx_status plx_render_forward(const plx_grid *grid, const plx_cameras *cams,
 
 /* Sec. 5.2, Eq. 4-11. Mapping adjoint: for the loss
  *   L = 1/M sum_valid |C - C_t|^2 + lambda_d/M sum_valid (D - D_t)^2
- * re-marches every valid ray, recomputes T_i and the prefix sums of Eq. 9-10
- * (nothing per sample is stored by the forward), and ADDS dL/d(value) into
- * `grad`.
+ * re-marches every valid ray (or, with a sample cache, visits the samples the
+ * forward kept), recomputes T_i and the prefix sums of Eq. 9-10, and ADDS
+ * dL/d(value) into `grad`.
  *   rgb_target   DEVICE float [n_rays][3]
  *   depth_target DEVICE float [n_rays] (see depth_is_z)
  *   rgb, depth   DEVICE float, the outputs of plx_render_forward for the

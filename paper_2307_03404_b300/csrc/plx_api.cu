@@ -524,13 +524,39 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
   return PLX_OK;
 }
 
+// The sample cache of opts (forward and grid adjoint only), laid out for
+// n = sample_rays rays: float4 [K][n], int32 [K][n], int32 [n].
+static plx_status set_sample_cache(const char* what, const plx_render_opts* o, Common& P) {
+  if (!o->sample_cache || o->sample_cap == 0) return PLX_OK;
+  if (o->sample_cap < 0) return fail(PLX_EINVAL, "%s: sample_cap < 0", what);
+  if (reinterpret_cast<uintptr_t>(o->sample_cache) % 16 != 0)
+    return fail(PLX_EINVAL, "%s: sample_cache must be 16-byte aligned", what);
+  if (o->sample_rays < P.ct.n_rays)
+    return fail(PLX_EINVAL, "%s: sample cache sized for %lld rays, call has %lld", what,
+                (long long)o->sample_rays, (long long)P.ct.n_rays);
+  const int64_t n = o->sample_rays, K = o->sample_cap;
+  char* base = static_cast<char*>(o->sample_cache);
+  P.o.cval = reinterpret_cast<float4*>(base);
+  P.o.ck = reinterpret_cast<int32_t*>(base + 16 * K * n);
+  P.o.ccount = reinterpret_cast<int32_t*>(base + 20 * K * n);
+  P.o.cn = n;
+  P.o.ccap = (int32_t)K;
+  return PLX_OK;
+}
+
 extern "C" {
+
+int64_t plx_sample_cache_bytes(int64_t n_rays, int32_t cap) {
+  if (n_rays < 0 || cap < 0) return -1;
+  return n_rays * (20 * (int64_t)cap + 4);
+}
 
 plx_status plx_render_forward(const plx_grid* g, const plx_cameras* cams, const plx_rays* rays,
                               const plx_render_opts* opts, float* rgb_out, float* depth_out,
                               float* state_out, int32_t* counts_out, void* stream) {
   Common P;
   plx_status st = build_common("render_forward", g, cams, rays, opts, -1, PLX_FINE_FORWARD, P);
+  if (st == PLX_OK) st = set_sample_cache("render_forward", opts, P);
   if (st != PLX_OK) return st;
   if (P.ct.n_rays > 0 && (!rgb_out || !depth_out))
     return fail(PLX_EINVAL, "render_forward: null rgb_out or depth_out");
@@ -546,6 +572,7 @@ plx_status plx_render_backward_grid(const plx_grid* g, const plx_cameras* cams,
                                     double* loss_out, void* stream) {
   Common P;
   plx_status st = build_common("render_backward_grid", g, cams, rays, opts, -1, PLX_FINE_ADJOINT, P);
+  if (st == PLX_OK) st = set_sample_cache("render_backward_grid", opts, P);
   if (st != PLX_OK) return st;
   if (P.ct.n_rays > 0 && (!rgb_target || !depth_target || !rgb || !depth || !grad))
     return fail(PLX_EINVAL, "render_backward_grid: null array argument");

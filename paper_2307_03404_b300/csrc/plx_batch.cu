@@ -82,7 +82,7 @@ k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
       sh_basis(r.dir, Y);
       float C[3], D, T;
       int n_all = 0, n_occ = 0;
-      march_forward<STORE, false>(P, r, Y, C, D, T, n_all, n_occ);
+      march_forward<STORE, false>(P, r, Y, C, D, T, n_all, n_occ, 0);
       const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
       float gC[3], e2 = 0.f;
 #pragma unroll

@@ -129,6 +129,13 @@ struct Opts {
   int32_t color_act;
   int32_t depth_is_z;
   int32_t dir_term;               // pose Jacobian: add the SH view-direction term
+  // sample cache (forward writes, grid adjoint reads; all null / 0 when off):
+  // kept sample j of ray row r at [j * cn + r]
+  float4* cval;                   // (sigma, c_r, c_g, c_b)
+  int32_t* ck;                    // sample index k
+  int32_t* ccount;                // [cn] samples with sigma > 0 per ray
+  int64_t cn;                     // rays of the call
+  int32_t ccap;                   // K
 };
 
 struct Common {

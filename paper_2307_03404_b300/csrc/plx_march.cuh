@@ -5,10 +5,13 @@
 
 namespace plx {
 
+// With the sample cache on (P.o.ccap > 0) the samples that composite are kept
+// for the grid adjoint: (sigma, colour) and k of the first ccap of them, and
+// their number, in row `out`.
 template <int STORE, bool COUNT>
 __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, const float Y[9],
                                               float C[3], float& D, float& T, int& n_all,
-                                              int& n_occ) {
+                                              int& n_occ, int64_t out) {
   const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
   int cx = -1, cy = -1, cz = -1;
   bool empty = true;
@@ -18,6 +21,7 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
   D = 0.f;
   T = 1.f;
   n_all = r.n;
+  int kept = 0;
   for (int k = 0; k < r.n; ++k) {
     const float kf = (float)k;
     int ix, iy, iz;
@@ -52,6 +56,14 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
       float dact;
       col[ch] = activate(a, P.o.color_act, dact);
     }
+    if (P.o.ccap > 0) {
+      if (kept < P.o.ccap) {
+        const int64_t at = (int64_t)kept * P.o.cn + out;
+        P.o.cval[at] = make_float4(sig, col[0], col[1], col[2]);
+        P.o.ck[at] = k;
+      }
+      ++kept;
+    }
     float alpha, keep;
     alpha_of(sig * r.dt, alpha, keep);
     const float wgt = T * alpha;
@@ -65,6 +77,7 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
       break;
     }
   }
+  if (P.o.ccap > 0) P.o.ccount[out] = kept;
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], C[ch]);
 }
@@ -122,6 +135,31 @@ __device__ __forceinline__ void carry_cell(float* __restrict__ grad, const int32
   }
 }
 
+// Leaves the current cell for the one (dx, dy, dz) away: if `carry` and the
+// step is to a face-adjacent cell, the shared face's sums move to their new
+// slots and the rest are flushed; otherwise all are flushed. Returns whether
+// carried sums remain in registers.
+__device__ __forceinline__ bool leave_cell(float* __restrict__ grad, const int32_t l[8],
+                                           float gs[8], float gc[8][3], const float Y[9], int dx,
+                                           int dy, int dz, bool carry) {
+  int step = -1;  // face-adjacent step: 0/1 = +x/-x, 2/3 = +y/-y, 4/5 = +z/-z
+  if (carry) {
+    if (dy == 0 && dz == 0) step = dx == 1 ? 0 : (dx == -1 ? 1 : -1);
+    else if (dx == 0 && dz == 0) step = dy == 1 ? 2 : (dy == -1 ? 3 : -1);
+    else if (dx == 0 && dy == 0) step = dz == 1 ? 4 : (dz == -1 ? 5 : -1);
+  }
+  switch (step) {
+    case 0: carry_cell<1, true>(grad, l, gs, gc, Y); break;
+    case 1: carry_cell<1, false>(grad, l, gs, gc, Y); break;
+    case 2: carry_cell<2, true>(grad, l, gs, gc, Y); break;
+    case 3: carry_cell<2, false>(grad, l, gs, gc, Y); break;
+    case 4: carry_cell<4, true>(grad, l, gs, gc, Y); break;
+    case 5: carry_cell<4, false>(grad, l, gs, gc, Y); break;
+    default: flush_cell(grad, l, gs, gc, Y); break;
+  }
+  return step >= 0;
+}
+
 template <int STORE>
 __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, const float Y[9],
                                                const float Cf[3], float Df, const float gC[3],
@@ -147,25 +185,8 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
     if (ix != cx || iy != cy || iz != cz) {
       const int esh = empty_block_shift(P.g, ix, iy, iz);
       const bool skip = esh >= 0;
-      if (dirty) {
-        const int dx = ix - cx, dy = iy - cy, dz = iz - cz;
-        int step = -1;  // face-adjacent step: 0/1 = +x/-x, 2/3 = +y/-y, 4/5 = +z/-z
-        if (!skip) {
-          if (dy == 0 && dz == 0) step = dx == 1 ? 0 : (dx == -1 ? 1 : -1);
-          else if (dx == 0 && dz == 0) step = dy == 1 ? 2 : (dy == -1 ? 3 : -1);
-          else if (dx == 0 && dy == 0) step = dz == 1 ? 4 : (dz == -1 ? 5 : -1);
-        }
-        switch (step) {
-          case 0: carry_cell<1, true>(grad, l, gs, gc, Y); break;
-          case 1: carry_cell<1, false>(grad, l, gs, gc, Y); break;
-          case 2: carry_cell<2, true>(grad, l, gs, gc, Y); break;
-          case 3: carry_cell<2, false>(grad, l, gs, gc, Y); break;
-          case 4: carry_cell<4, true>(grad, l, gs, gc, Y); break;
-          case 5: carry_cell<4, false>(grad, l, gs, gc, Y); break;
-          default: flush_cell(grad, l, gs, gc, Y); break;
-        }
-        dirty = step >= 0;  // carried sums still have to reach memory
-      }
+      if (dirty)  // carried sums still have to reach memory
+        dirty = leave_cell(grad, l, gs, gc, Y, ix - cx, iy - cy, iz - cz, !skip);
       cx = ix; cy = iy; cz = iz;
       if (skip) {
         empty = true;
@@ -214,6 +235,76 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
     dirty = true;
     T = Tn;
     if (T < P.o.stop_T) break;
+  }
+  if (dirty) flush_cell(grad, l, gs, gc, Y);
+}
+
+// The same adjoint over the n_kept samples the forward kept in the sample
+// cache (row `out`): sigma and colour are read back instead of interpolated,
+// so no cell record is gathered and no empty stretch is marched; only the
+// links of the cells holding those samples are loaded, for the scatter. The
+// per-sample arithmetic is march_backward's, in the same order.
+__device__ __forceinline__ void march_backward_cached(const Common& P, const RayF& r,
+                                                      const float Y[9], const float Cf[3],
+                                                      float Df, const float gC[3], float gD,
+                                                      float* __restrict__ grad, int64_t out,
+                                                      int n_kept) {
+  const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
+  int cx = -1, cy = -1, cz = -1;
+  bool dirty = false;
+  int32_t l[8];
+  float gs[8], gc[8][3];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) clear_corner(gs[c], gc[c]);
+  float S[3] = {0.f, 0.f, 0.f}, SD = 0.f, T = 1.f;
+  const float dt = r.dt;
+  const bool ident = P.o.color_act == PLX_ACT_IDENTITY;
+  for (int j = 0; j < n_kept; ++j) {
+    const int64_t at = (int64_t)j * P.o.cn + out;
+    const float4 v = __ldg(P.o.cval + at);
+    const int k = __ldg(P.o.ck + at);
+    const float kf = (float)k;
+    int ix, iy, iz;
+    float fx, fy, fz;
+    sample_axis(r.B[0], r.S[0], k, rm2x, ix, fx);
+    sample_axis(r.B[1], r.S[1], k, rm2y, iy, fy);
+    sample_axis(r.B[2], r.S[2], k, rm2z, iz, fz);
+    if (ix != cx || iy != cy || iz != cz) {
+      if (dirty) dirty = leave_cell(grad, l, gs, gc, Y, ix - cx, iy - cy, iz - cz, true);
+      cx = ix; cy = iy; cz = iz;
+      load_links(P.g, ix, iy, iz, l);
+    }
+    float w[8];
+    corner_weights(fx, fy, fz, w);
+    const float sig = v.x;  // > 0: only compositing samples are kept
+    const float col[3] = {v.y, v.z, v.w};
+    float dact[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) dact[ch] = ident ? 1.f : col[ch] * (1.f - col[ch]);
+    float alpha, keep;
+    alpha_of(sig * dt, alpha, keep);
+    const float wgt = T * alpha;
+    const float Tn = T * keep;
+    const float t = fmaf(kf, dt, r.t0);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) S[ch] = fmaf(wgt, col[ch], S[ch]);
+    SD = fmaf(wgt, t, SD);
+    // Eq. 9 and Eq. 10
+    float dsig = gD * dt * (t * Tn - Df + SD);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) dsig = fmaf(gC[ch] * dt, col[ch] * Tn - Cf[ch] + S[ch], dsig);
+    // Eq. 8 through the colour activation
+    float dch[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) dch[ch] = gC[ch] * wgt * dact[ch];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      gs[c] = fmaf(w[c], dsig, gs[c]);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) gc[c][ch] = fmaf(w[c], dch[ch], gc[c][ch]);
+    }
+    dirty = true;
+    T = Tn;
   }
   if (dirty) flush_cell(grad, l, gs, gc, Y);
 }

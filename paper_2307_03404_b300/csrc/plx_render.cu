@@ -7,8 +7,9 @@
 //
 // Adjoint: the ray is marched again with the forward's C and D, recomputing
 // T_i, T_{i+1}, w_i and the inclusive prefix sums S_i = sum_{j<=i} w_j c_j,
-// SD_i = sum_{j<=i} w_j t_j (nothing per sample is stored between the two
-// passes). Per sample, Eq. 8 gives dL/dc_i = g_C w_i and Eq. 9-10 give
+// SD_i = sum_{j<=i} w_j t_j. With a sample cache the forward keeps the index,
+// density and colour of each compositing sample (up to K per ray) and the
+// adjoint visits just those; rays with more re-march in full. Per sample, Eq. 8 gives dL/dc_i = g_C w_i and Eq. 9-10 give
 //   dL/dsigma_i = g_C . delta (c_i T_{i+1} - C + S_i) + g_D delta (t_i T_{i+1} - D + SD_i).
 // The gradients are accumulated per corner in registers while the ray stays in
 // one cell, as (d density, d projected colour per channel); SH gradients are
@@ -42,7 +43,7 @@ k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __re
   sh_basis(r.dir, Y);
   float C[3], D, T;
   int n_all = 0, n_occ = 0;
-  march_forward<STORE, COUNT>(P, r, Y, C, D, T, n_all, n_occ);
+  march_forward<STORE, COUNT>(P, r, Y, C, D, T, n_all, n_occ, id.out);
   rgb[3 * id.out] = C[0];
   rgb[3 * id.out + 1] = C[1];
   rgb[3 * id.out + 2] = C[2];
@@ -79,7 +80,9 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
     RayF r;
     setup_ray(P, id, r, lane);
     const unsigned long long M = *Mc;
-    if (id.valid && M > 0) {
+    // with a sample cache this launch re-marches only the rays it could not hold
+    const bool todo = P.o.ccap == 0 || (id.valid && __ldg(P.o.ccount + id.out) > P.o.ccap);
+    if (id.valid && M > 0 && todo) {
       const float dz = __ldg(depth_t + id.out);
       if (depth_valid(dz)) {
         float Y[9];
@@ -105,6 +108,59 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
   }
   if (loss_out) {
     // per warp: FP64 sum of the rays' squared residuals, one atomic per warp
+    double s = (double)loss;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const unsigned long long M = *Mc;
+    if (lane == 0 && s != 0.0) atomicAdd(loss_out, s / (double)M);
+    if (blockIdx.x == 0 && threadIdx.x == 0) loss_out[1] = (double)M;
+  }
+}
+
+// The grid adjoint from the sample cache: every valid ray's loss term, and the
+// gradients of the rays whose compositing samples all fit in it.
+template <int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
+k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
+                       const float* __restrict__ depth_t, const float* __restrict__ rgb,
+                       const float* __restrict__ depth, float* __restrict__ grad,
+                       double* __restrict__ loss_out, const unsigned long long* __restrict__ Mc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  float loss = 0.f;
+  if (tile < P.ct.n_tiles) {
+    const RayId id = ray_of(P, tile, lane);
+    RayF r;
+    setup_ray(P, id, r, lane);
+    const unsigned long long M = *Mc;
+    if (id.valid && M > 0) {
+      const float dz = __ldg(depth_t + id.out);
+      if (depth_valid(dz)) {
+        const float invM = (float)(1.0 / (double)M);
+        const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
+        float Cf[3], gC[3];
+        float e2 = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          Cf[ch] = __ldg(rgb + 3 * id.out + ch);
+          const float e = Cf[ch] - __ldg(rgb_t + 3 * id.out + ch);
+          e2 = fmaf(e, e, e2);
+          gC[ch] = 2.f * e * invM;
+        }
+        const float Df = __ldg(depth + id.out);
+        const float eD = Df - Dt;
+        loss = fmaf(P.o.lambda_d * eD, eD, e2);
+        const float gD = 2.f * P.o.lambda_d * eD * invM;
+        const int n_kept = __ldg(P.o.ccount + id.out);
+        if (n_kept <= P.o.ccap) {
+          float Y[9];
+          sh_basis(r.dir, Y);
+          march_backward_cached(P, r, Y, Cf, Df, gC, gD, grad, id.out, n_kept);
+        }
+      }
+    }
+  }
+  if (loss_out) {
     double s = (double)loss;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -140,9 +196,19 @@ void launch_backward_grid(int store, int minb, const Common& P, const float* rgb
   }
   if (P.ct.n_tiles == 0) return;
   const unsigned blocks = (unsigned)((P.ct.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  double* loss_full = loss_out;
+  if (P.o.ccap > 0) {  // the cache's rays (and every loss term), then the overflow
+    if (minb == 1)
+      k_backward_grid_cached<1><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad,
+                                                          loss_out, M);
+    else
+      k_backward_grid_cached<2><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad,
+                                                          loss_out, M);
+    loss_full = nullptr;
+  }
 #define PLX_BWD(S, M_)                                                                   \
   k_backward_grid<S, M_><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad, \
-                                                  loss_out, M)
+                                                  loss_full, M)
   PLX_DISPATCH_SM(store, minb, PLX_BWD);
 #undef PLX_BWD
 }

@@ -80,6 +80,7 @@ class MapConfig:
     band: float = 2.0
     seed: int = 7
     sort_rays: bool = True      # order each step's random rays for coherence
+    sample_cache: bool = True   # forward keeps compositing samples for the adjoint
 
 
 @dataclasses.dataclass
@@ -127,6 +128,7 @@ def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: 
     grad = torch.zeros(dg.n, plx.GRAD_STRIDE, device="cuda")
     losses = torch.zeros(cfg.iters, 2, dtype=torch.float64, device="cuda")
     fw = None
+    cache, oc = None, opts
     widths = torch.tensor([w for w, _ in cams.sizes], device="cuda")
     for it in range(cfg.iters):
         rows = torch.randint(0, total, (cfg.rays_per_step,), generator=gen, device="cuda")
@@ -143,8 +145,13 @@ def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: 
         cam_id, pix = cam_id.to(torch.int32), pix.to(torch.int32)
         rays = (cam_id, pix)
         rgb_t, depth_t = rgb[rows], depth[rows]
-        fw = plx.render_forward(dg.grid, cams, opts, rays=rays, out=fw)
-        plx.render_backward_grid(dg.grid, cams, opts, rgb_t, depth_t, fw["rgb"], fw["depth"],
+        if it == 0 and cfg.sample_cache:
+            # sized on the first ray set with headroom; a later ray with more
+            # compositing samples than the cap is re-marched by the adjoint
+            cache = plx.SampleCache.sized_for(dg.grid, cams, opts, rays=rays, headroom=1.5)
+            oc = cache.opts(opts)
+        fw = plx.render_forward(dg.grid, cams, oc, rays=rays, out=fw)
+        plx.render_backward_grid(dg.grid, cams, oc, rgb_t, depth_t, fw["rgb"], fw["depth"],
                                  rays=rays, grad=grad, loss=losses[it])
         f = it / max(1, cfg.iters - 1)
         lr_d = cfg.lr_density * (cfg.lr_density_final / cfg.lr_density) ** f

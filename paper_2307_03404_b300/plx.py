@@ -73,7 +73,9 @@ class LaunchConfig(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("step", C.c_double), ("near_t", C.c_double), ("stop_T", C.c_double),
                 ("bg", C.c_float * 3), ("lambda_d", C.c_float), ("max_samples", C.c_int32),
-                ("color_act", C.c_int32), ("depth_is_z", C.c_int32), ("pose_flags", C.c_int32)]
+                ("color_act", C.c_int32), ("depth_is_z", C.c_int32), ("pose_flags", C.c_int32),
+                ("sample_cache", C.c_void_p), ("sample_cap", C.c_int32),
+                ("sample_rays", C.c_int64)]
 
 
 SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload",
@@ -81,7 +83,7 @@ SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload"
            "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
            "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch",
            "plx_grid_rmsprop", "plx_track_adam_step", "plx_grid_get_config",
-           "plx_grid_set_config", "plx_grid_grow", "plx_pose_step_lm"]
+           "plx_grid_set_config", "plx_grid_grow", "plx_pose_step_lm", "plx_sample_cache_bytes"]
 
 
 def _load():
@@ -123,6 +125,8 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = C.c_int
+    lib.plx_sample_cache_bytes.argtypes = [I64, I32]
+    lib.plx_sample_cache_bytes.restype = C.c_int64
     return lib
 
 
@@ -310,6 +314,57 @@ def make_opts(step, near=0.0, stop_T=0.0, bg=(0.0, 0.0, 0.0), lambda_d=1.0,
     o.depth_is_z = int(bool(depth_is_z))
     o.pose_flags = POSE_VIEW_DIR if view_dir else 0
     return o
+
+
+def sample_cache_bytes(n_rays, cap):
+    """plx_sample_cache_bytes: bytes of a sample cache for n_rays rays, cap each."""
+    return int(_lib.plx_sample_cache_bytes(int(n_rays), int(cap)))
+
+
+class SampleCache:
+    """A sample cache (plx_render_opts.sample_cache) for calls over ``n_rays``
+    rays: the forward keeps up to ``cap`` compositing samples per ray and the
+    grid adjoint of the same rays reads them back. ``opts(o)`` returns a copy
+    of the options naming it; ``counts()`` the number of compositing samples
+    per ray of the last forward (may exceed cap)."""
+
+    def __init__(self, n_rays, cap, device="cuda"):
+        self.n_rays, self.cap = int(n_rays), int(cap)
+        nbytes = sample_cache_bytes(self.n_rays, self.cap)
+        if nbytes < 0:
+            raise ValueError("n_rays and cap must be >= 0")
+        # float32 storage: the base is 16-byte aligned as the ABI asks
+        self.buf = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=device)
+
+    @classmethod
+    def sized_for(cls, grid, cams, opts, rays=None, max_bytes=None, headroom=1.0, stream=None):
+        """A cache whose cap holds every ray of this call: one probe forward
+        with cap 1 counts each ray's compositing samples, and cap is their
+        maximum times ``headroom`` (for later calls on other rays or grid
+        values) rounded up to a multiple of 8, at most what fits in
+        ``max_bytes`` (default a quarter of the free device memory)."""
+        n = cams.n_pixels() if rays is None else int(rays[1].shape[0])
+        probe = cls(n, 1)
+        render_forward(grid, cams, probe.opts(opts), rays=rays, state=False, stream=stream)
+        need = int(probe.counts().max().item()) if n > 0 else 0
+        cap = max(8, (int(need * headroom) + 7) // 8 * 8)
+        if max_bytes is None:
+            max_bytes = torch.cuda.mem_get_info()[0] // 4
+        while cap > 8 and sample_cache_bytes(n, cap) > max_bytes:
+            cap -= 8
+        del probe
+        return cls(n, cap)
+
+    def opts(self, o):
+        c = RenderOpts.from_buffer_copy(o)
+        c.sample_cache = self.buf.data_ptr() if self.cap > 0 else None
+        c.sample_cap = self.cap
+        c.sample_rays = self.n_rays
+        return c
+
+    def counts(self):
+        off = 5 * self.cap * self.n_rays  # float4 [cap][n] then int32 [cap][n], in 4-byte words
+        return self.buf[off:off + self.n_rays].view(torch.int32)
 
 
 def opts_from_dict(d):

@@ -72,6 +72,8 @@ int main(void) {
   S(plx_rays); P(plx_rays, cam_id); P(plx_rays, pixel);
   S(plx_render_opts); P(plx_render_opts, bg); P(plx_render_opts, lambda_d);
   P(plx_render_opts, max_samples); P(plx_render_opts, depth_is_z);
+  P(plx_render_opts, sample_cache); P(plx_render_opts, sample_cap);
+  P(plx_render_opts, sample_rays);
   return 0;
 }
 """)
@@ -110,6 +112,18 @@ def test_argument_errors_are_reported_without_touching_the_gpu(lib):
     assert b"damping" in lib.plx_last_error()
     assert lib.plx_render_forward(None, None, None, None, None, None, None, None, None) == 1
     assert lib.plx_grid_destroy(None) == 0
+
+
+def test_sample_cache_size(lib):
+    """float4 [K][n] + int32 [K][n] + int32 [n]; -1 for a negative argument."""
+    from paper_2307_03404_b300 import plx
+
+    assert plx.sample_cache_bytes(0, 5) == 0
+    assert plx.sample_cache_bytes(7, 0) == 28
+    assert plx.sample_cache_bytes(2_457_600, 64) == 2_457_600 * (64 * 16 + 64 * 4 + 4)
+    assert plx.sample_cache_bytes(-1, 4) == -1 and plx.sample_cache_bytes(4, -1) == -1
+    o = plx.make_opts(0.1)
+    assert o.sample_cache is None and o.sample_cap == 0
 
 
 def test_grid_grow_argument_errors(lib):

@@ -165,15 +165,26 @@ def sphere_targets(sphere, depth_is_z):
     return rgb_t, depth_t
 
 
+@pytest.mark.parametrize("cache_cap", [None, 256, 3])
 @pytest.mark.parametrize("depth_is_z,act,bg", [(False, "sigmoid", (0, 0, 0)),
                                                 (True, "sigmoid", (0.3, 0.2, 0.1)),
                                                 (True, "identity", (0.0, 0.5, 0.0))])
-def test_backward_grid_sphere_scene(sphere, depth_is_z, act, bg):
+def test_backward_grid_sphere_scene(sphere, depth_is_z, act, bg, cache_cap):
+    """Without a sample cache, with one that holds every ray, and with one so
+    small that most rays overflow it and re-march (both paths in one call)."""
     g, cam, _, opts = sphere
     opts = dict(opts, depth_is_z=depth_is_z, color_act=act, bg=bg, lambda_d=0.7)
     rgb_t, depth_t = sphere_targets(sphere, depth_is_z)
     case = GpuCase(g, [cam])
-    gd, gs, gpad, loss = case.backward_grid(opts, rgb_t, depth_t)
+    gd, gs, gpad, loss = case.backward_grid(opts, rgb_t, depth_t, cache_cap=cache_cap)
+    if cache_cap is not None:
+        kept = case.cache.counts().cpu().numpy()
+        fwd = case.forward(opts)
+        assert np.all(kept >= 0) and np.all(kept <= fwd["counts"][:, 1])
+        if cache_cap == 256:
+            assert kept.max() <= 256
+        else:
+            assert (kept > cache_cap).mean() > 0.2 and (kept[kept > 0] <= cache_cap).any()
     ref = oracle.grad_grid(g, [cam], opts, rgb_t, depth_t)
     assert loss[1] == ref.M
     assert abs(loss[0] - ref.loss) <= 1e-5 * ref.loss
@@ -182,7 +193,8 @@ def test_backward_grid_sphere_scene(sphere, depth_is_z, act, bg):
     assert np.all(gpad == 0)
 
 
-def test_backward_grid_sparse_list_mode_accumulates():
+@pytest.mark.parametrize("cache_cap", [None, 8])
+def test_backward_grid_sparse_list_mode_accumulates(cache_cap):
     g = scenes.tiny_grid(7, seed=31, alloc_frac=0.6, sigma_mean=2.0, sigma_std=2.0)
     cams = tiny_cams()
     opts = dict(step=0.11, bg=(0.2, 0.1, 0.0), lambda_d=0.4)
@@ -194,7 +206,7 @@ def test_backward_grid_sparse_list_mode_accumulates():
     depth_t = rng.uniform(0.5, 4, 100).astype(np.float32)
     depth_t[::9] = -1.0
     case = GpuCase(g, cams)
-    gd, gs, _, loss = case.backward_grid(opts, rgb_t, depth_t, rays=rays)
+    gd, gs, _, loss = case.backward_grid(opts, rgb_t, depth_t, rays=rays, cache_cap=cache_cap)
     ref = oracle.grad_grid(g, cams, opts, rgb_t, depth_t, rays=rays)
     assert loss[1] == ref.M
     assert abs(loss[0] - ref.loss) <= 1e-5 * ref.loss
