@@ -98,16 +98,27 @@ def measured_profile(kernel, workload, storage):
     return None
 
 
-def measured_traffic(kernel, workload, storage):
+def _per_launch(rec, key, n_rays):
+    """A per-launch ncu figure scaled to a launch over n_rays rays when the
+    capture ran on fewer (a smaller case of the same kernel, see
+    rays_per_launch in the record)."""
+    v = rec[key]
+    if n_rays and rec.get("rays_per_launch"):
+        v = v * n_rays / rec["rays_per_launch"]
+    return v
+
+
+def measured_traffic(kernel, workload, storage, n_rays=None):
     rec = measured_profile(kernel, workload, storage)
-    return rec["dram_bytes_per_launch"] if rec else None
+    return _per_launch(rec, "dram_bytes_per_launch", n_rays) if rec else None
 
 
-def issue_roofline(kernel, ms, storage, clocks):
+def issue_roofline(kernel, ms, storage, clocks, n_rays=None):
     """Instruction-issue utilisation of a kernel: warp instructions per launch
-    (ncu, profiles/traffic.json, valid for the current sources) over the live
-    launch time, against one warp instruction per clock per SM sub-partition
-    (4 per SM) at the SM clock sampled during the run."""
+    (ncu, profiles/traffic.json, valid for the current sources, scaled to
+    n_rays rays) over the live launch time, against one warp instruction per
+    clock per SM sub-partition (4 per SM) at the SM clock sampled during the
+    run."""
     import torch
 
     rec = measured_profile(kernel, "room256", storage)
@@ -116,9 +127,10 @@ def issue_roofline(kernel, ms, storage, clocks):
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2032.0
     peak = sms * 4 * mhz * 1e6
-    achieved = rec["warp_instructions_per_launch"] / (ms / 1e3)
+    wi = _per_launch(rec, "warp_instructions_per_launch", n_rays)
+    achieved = wi / (ms / 1e3)
     return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s",
-            "frac": achieved / peak, "warp_instructions_per_launch": rec["warp_instructions_per_launch"],
+            "frac": achieved / peak, "warp_instructions_per_launch": wi,
             "peak_basis": f"{sms} SMs x 4 sub-partitions x 1 warp instruction per clock x {mhz:.0f} MHz"}
 
 
@@ -186,14 +198,16 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- workload
-def mapping_workload(world, rank):
+def mapping_workload(world, rank, frames=FRAMES_PER_RANK):
+    """room256 and this rank's keyframes; ``frames`` < 8 keeps only the first
+    of them (a smaller case of the same kernels, for profiler captures)."""
     from paper_2307_03404_b300 import scenes
 
     R, occ, npr, seed = scenes.WORKLOADS["room256"]
     t = time.time()
     sc = scenes.room_scene(R, occ, npr, seed)
     cams_all = scenes.room_cameras(sc, FRAMES_PER_RANK * world, seed + 1)
-    cams = [cams_all[i] for i in shard_frames(world, rank)]
+    cams = [cams_all[i] for i in shard_frames(world, rank)][:frames]
     rgb_t, depth_t = scenes.sensor_frames(sc, cams, seed + 2 + rank)
     opts = dict(step=0.5 * float(sc.grid.h[0]), lambda_d=1.0, depth_is_z=True)
     log(f"[bench] room256 scene + frames in {time.time() - t:.1f}s, n_alloc {sc.grid.n_alloc}")
@@ -264,7 +278,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    sc, cams_np, rgb_np, depth_np, opts = mapping_workload(world, rank)
+    sc, cams_np, rgb_np, depth_np, opts = mapping_workload(world, rank, args.map_frames)
     n_rays = rgb_np.shape[0]
     cams = plx.CameraSet(cams_np)
     o_plain = plx.opts_from_dict(opts)
@@ -435,7 +449,7 @@ def run_ours(args):
     # once, its FP32 gradient row read and written once, its link once
     rec_b = 128 if args.storage == "f32" else 64
     compulsory = main["touched"] * (rec_b + 2 * 112 + 4)
-    traffic = measured_traffic(dom, "room256", args.storage)
+    traffic = measured_traffic(dom, "room256", args.storage, n_rays)
     if traffic:
         dram_gbs = traffic / (dom_ms / 1e3) / 1e9
     line = {
@@ -447,7 +461,7 @@ def run_ours(args):
                        sample_cache=cache_note(main, n_rays)),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": measured_traffic(dom, "room256", args.storage),
+                     "traffic": traffic,
                      "model": "no-reuse byte model: 32 B of links per marched sample and pass, "
                               "896 B (f32) / 448 B (16-bit) per gathered sample with an "
                               "allocated corner, 32-36 B of per-ray I/O; with the sample "
@@ -466,7 +480,7 @@ def run_ours(args):
                      "touched_vertices": main["touched"],
                      "compulsory_bytes_per_launch": compulsory,
                      "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9,
-                     "issue": issue_roofline(dom, dom_ms, args.storage, clocks)},
+                     "issue": issue_roofline(dom, dom_ms, args.storage, clocks, n_rays)},
         "e2e": {"value": rays_job / (t_e2e / 1e3), "unit": "rays/s",
                 "h2d_bytes_per_step": main["h2d"], "d2h_bytes_per_step": main["d2h"],
                 "timing": "K steps as one region (first copy to last loss read); copies of "
@@ -951,6 +965,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
+    ap.add_argument("--map-frames", type=int, default=FRAMES_PER_RANK,
+                    help="keyframes per rank of the mapping workload (8; fewer only for "
+                         "profiler captures)")
     ap.add_argument("--sample-cache", default="fit",
                     help='"fit" (sized so no ray overflows), "off", or samples per ray')
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
