@@ -5,9 +5,10 @@
 of the grid values. Its gradient is the analytic adjoint of Eq. 6-10
 (``plx_render_backward_grid``). The loss and the gradient come out of the same
 pass (the adjoint kernel produces both), so the forward stores the gradient
-and the backward only scales it by the incoming gradient: there is no second
-march. Per-sample transmittance is never stored; the adjoint kernel recomputes
-it.
+and the backward only scales it by the incoming gradient. Options naming a
+sample cache (``plx.SampleCache.opts``) make the adjoint read back the
+forward's compositing samples instead of re-marching the rays; per-sample
+transmittance is recomputed either way.
 """
 from __future__ import annotations
 

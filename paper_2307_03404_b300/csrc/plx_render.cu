@@ -75,13 +75,15 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   float loss = 0.f;
-  if (tile < P.ct.n_tiles) {
-    const RayId id = ray_of(P, tile, lane);
+  // with a sample cache this launch re-marches only the rays it could not
+  // hold, and a warp without such a ray leaves at once (the loss is then
+  // summed by the cached launch, loss_out is null here)
+  const RayId id = ray_of(P, tile < P.ct.n_tiles ? tile : 0, lane);
+  const bool todo = P.o.ccap == 0 || (id.valid && __ldg(P.o.ccount + id.out) > P.o.ccap);
+  if (tile < P.ct.n_tiles && __any_sync(0xffffffffu, todo)) {
     RayF r;
     setup_ray(P, id, r, lane);
     const unsigned long long M = *Mc;
-    // with a sample cache this launch re-marches only the rays it could not hold
-    const bool todo = P.o.ccap == 0 || (id.valid && __ldg(P.o.ccount + id.out) > P.o.ccap);
     if (id.valid && M > 0 && todo) {
       const float dz = __ldg(depth_t + id.out);
       if (depth_valid(dz)) {
