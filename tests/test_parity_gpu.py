@@ -442,8 +442,9 @@ def test_16bit_storage_error(sphere, storage):
     np.testing.assert_array_equal(s2.cpu().numpy(), gr.sh)
 
 
+@pytest.mark.parametrize("cache_cap", [None, 256])
 @pytest.mark.parametrize("storage", ["bf16", "f16", "f32_bf16"])
-def test_16bit_storage_adjoint_and_pose(sphere, storage):
+def test_16bit_storage_adjoint_and_pose(sphere, storage, cache_cap):
     """Grid adjoint and pose system with 16-bit storage against the oracle on
     the same rounded values: FP32-level agreement (the kernels decode the
     records exactly; only the rounding of the stored values differs from
@@ -458,7 +459,7 @@ def test_16bit_storage_adjoint_and_pose(sphere, storage):
     tg = oracle.render(gp, [cam], opts)
     rgb_t, depth_t = tg.rgb.astype(np.float32), tg.depth.astype(np.float32)
     case = GpuCase(g, [cam], storage=storage)
-    gd, gs, _, loss = case.backward_grid(opts, rgb_t, depth_t)
+    gd, gs, _, loss = case.backward_grid(opts, rgb_t, depth_t, cache_cap=cache_cap)
     ref = oracle.grad_grid(gr, [cam], opts, rgb_t, depth_t)
     assert loss[1] == ref.M and abs(loss[0] - ref.loss) <= 1e-5 * ref.loss
     assert norm_err(gd, ref.grad_density) <= TOL_GRAD
@@ -467,6 +468,36 @@ def test_16bit_storage_adjoint_and_pose(sphere, storage):
     case.cams.poses.copy_(torch.tensor(T0.reshape(1, 12), device="cuda"))
     H, b, _ = case.backward_pose(opts, 0, rgb_t, depth_t)
     rp = oracle.pose_jacobian(gr, [cam.with_pose(T0)], opts, rgb_t, depth_t)
+    assert norm_err(H, rp.H) <= TOL_GRAD and norm_err(b, rp.b) <= TOL_GRAD
+
+
+@pytest.mark.parametrize("cache_cap", [None, 256])
+def test_stop_T_forward_adjoint_and_pose(sphere, cache_cap):
+    """Early termination (stop_T > 0): every kernel ends a ray after the
+    sample that takes T below stop_T, as the oracle does; the grid adjoint
+    with and without a sample cache, and the pose Jacobian (which then takes
+    its thread-per-ray form)."""
+    g, cam, gp, opts = sphere
+    opts = dict(opts, depth_is_z=False, lambda_d=0.7, stop_T=0.02)
+    case = GpuCase(g, [cam])
+    got = case.forward(opts)
+    ref = oracle.render(g, [cam], opts)
+    full = oracle.render(g, [cam], dict(opts, stop_T=0.0))
+    assert (ref.n_marched < full.n_marched).mean() > 0.2   # the stop does bite
+    np.testing.assert_array_equal(got["counts"][:, 0], ref.n_marched)
+    assert rel_err(got["rgb"], ref.rgb) <= TOL_FWD
+    assert rel_err(got["depth"], ref.depth) <= TOL_FWD
+    tg = oracle.render(gp, [cam], opts)
+    rgb_t, depth_t = tg.rgb.astype(np.float32), tg.depth.astype(np.float32)
+    gd, gs, _, loss = case.backward_grid(opts, rgb_t, depth_t, cache_cap=cache_cap)
+    rg = oracle.grad_grid(g, [cam], opts, rgb_t, depth_t)
+    assert loss[1] == rg.M and abs(loss[0] - rg.loss) <= 1e-5 * rg.loss
+    assert norm_err(gd, rg.grad_density) <= TOL_GRAD
+    assert norm_err(gs, rg.grad_sh) <= TOL_GRAD
+    T0 = scenes.perturb_pose(cam.T_wc, 0.02, 1.0, np.random.default_rng(4))
+    case.cams.poses.copy_(torch.tensor(T0.reshape(1, 12), device="cuda"))
+    H, b, _ = case.backward_pose(opts, 0, rgb_t, depth_t)
+    rp = oracle.pose_jacobian(g, [cam.with_pose(T0)], opts, rgb_t, depth_t)
     assert norm_err(H, rp.H) <= TOL_GRAD and norm_err(b, rp.b) <= TOL_GRAD
 
 
