@@ -715,10 +715,25 @@ def run_batch_bench(args, barrier):
 
     for storage in ("bf16", "f32"):
         grid = plx.Grid.from_scene(sc.grid, storage)
+        # sample caches (untimed set-up): per mapping ray for the separate
+        # calls, per thread slot for the batched launch, K from a probe forward
+        om = ob = o
+        sep_cache = bat_cache = None  # the other storage's caches go first
+        torch.cuda.empty_cache()
+        cache_note_b = "off"
+        if args.sample_cache != "off":
+            sep_cache = plx.SampleCache.sized_for(grid, map_cams, o)
+            bat_cache = plx.SampleCache.for_batch(sep_cache.cap)
+            om, ob = sep_cache.opts(o), bat_cache.opts(o)
+            cache_note_b = (f"K = {sep_cache.cap}: the batched launch keeps a ray's samples in its "
+                            f"thread's row ({bat_cache.n_rays} rows, "
+                            f"{plx.sample_cache_bytes(bat_cache.n_rays, bat_cache.cap) / 1e9:.2f} GB); "
+                            f"the separate calls per mapping ray "
+                            f"({plx.sample_cache_bytes(sep_cache.n_rays, sep_cache.cap) / 1e9:.1f} GB)")
         if not args.no_tune:
             from paper_2307_03404_b300 import autotune
 
-            autotune.tune_batch(grid, cams, work, o, rgb_t, depth_t, reps=2,
+            autotune.tune_batch(grid, cams, work, ob, rgb_t, depth_t, reps=2,
                                 cache=os.path.join("/tmp", f"plx_tuning_{os.getpid()}.json"))
         grad = torch.zeros(grid.n_alloc, plx.GRAD_STRIDE, device="cuda")
         mloss = torch.empty(2, device="cuda", dtype=torch.float64)
@@ -728,17 +743,18 @@ def run_batch_bench(args, barrier):
 
         def batch():
             grad.zero_()
-            plx.render_batch(grid, cams, work, o, rgb_t, depth_t, grad=grad, map_loss=mloss, out=bo)
+            plx.render_batch(grid, cams, work, ob, rgb_t, depth_t, grad=grad, map_loss=mloss,
+                             out=bo)
 
-        fw = plx.render_forward(grid, map_cams, o)
+        fw = plx.render_forward(grid, map_cams, om)
         po = (torch.empty(6, 6, device="cuda", dtype=torch.float64),
               torch.empty(6, device="cuda", dtype=torch.float64),
               torch.empty(2, device="cuda", dtype=torch.float64))
 
         def separate():
             grad.zero_()
-            plx.render_forward(grid, map_cams, o, out=fw)
-            plx.render_backward_grid(grid, map_cams, o, rgb_m, depth_m, fw["rgb"], fw["depth"],
+            plx.render_forward(grid, map_cams, om, out=fw)
+            plx.render_backward_grid(grid, map_cams, om, rgb_m, depth_m, fw["rgb"], fw["depth"],
                                      grad=grad, loss=mloss)
             for k, (r_, d_) in enumerate(trk):
                 plx.render_backward_pose(grid, trk_cams, k, o, r_, d_, out=po)
@@ -746,9 +762,9 @@ def run_batch_bench(args, barrier):
         ms_b = timed(batch, max(2, args.steps // 2), args.warmup)
         ms_s = timed(separate, max(2, args.steps // 2), args.warmup)
         out[storage] = {"value": rows / (ms_b / 1e3), "ms_per_batch": ms_b,
-                        "launch_config": grid.get_config(),
+                        "launch_config": grid.get_config(), "sample_cache": cache_note_b,
                         "separate_calls": {"value": rows / (ms_s / 1e3), "ms": ms_s,
-                                           "launches": 3 + 32}}
+                                           "launches": (4 if om is not o else 3) + 32}}
         # the mapping optimiser on this grid (Sec. 5.4 RMSProp, one pass over
         # all records, gradients and state): a plain streaming kernel, timed
         # against the copy bandwidth

@@ -159,7 +159,12 @@ typedef struct {
  * call must name the same cache and K, grid contents, cameras, rays and opts
  * as the forward that filled it (nothing checks this); without a cache it
  * re-marches every ray. Both ways give the same gradients up to the order of
- * floating-point sums. */
+ * floating-point sums.
+ * plx_render_batch uses the same layout with thread slots for rows: a mapping
+ * ray keeps its samples in the row of the thread that marches it, between
+ * that thread's forward and adjoint, and threads at or past sample_rays
+ * re-march. At most 2 x 256 threads per SM are resident in that launch, so
+ * sample_rays = 512 x (SM count) covers every thread. */
 int64_t plx_sample_cache_bytes(int64_t n_rays, int32_t cap); /* -1 if either < 0 */
 
 const char *plx_last_error(void);

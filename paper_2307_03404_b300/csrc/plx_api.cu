@@ -524,14 +524,17 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
   return PLX_OK;
 }
 
-// The sample cache of opts (forward and grid adjoint only), laid out for
-// n = sample_rays rays: float4 [K][n], int32 [K][n], int32 [n].
-static plx_status set_sample_cache(const char* what, const plx_render_opts* o, Common& P) {
+// The sample cache of opts, laid out for n = sample_rays rows: float4 [K][n],
+// int32 [K][n], int32 [n]. Rows are rays (forward and grid adjoint: n must
+// cover the call's rays) or, with per_ray false, thread slots (batched launch).
+static plx_status set_sample_cache(const char* what, const plx_render_opts* o, Common& P,
+                                   bool per_ray = true) {
   if (!o->sample_cache || o->sample_cap == 0) return PLX_OK;
   if (o->sample_cap < 0) return fail(PLX_EINVAL, "%s: sample_cap < 0", what);
   if (reinterpret_cast<uintptr_t>(o->sample_cache) % 16 != 0)
     return fail(PLX_EINVAL, "%s: sample_cache must be 16-byte aligned", what);
-  if (o->sample_rays < P.ct.n_rays)
+  if (o->sample_rays < 0) return fail(PLX_EINVAL, "%s: sample_rays < 0", what);
+  if (per_ray && o->sample_rays < P.ct.n_rays)
     return fail(PLX_EINVAL, "%s: sample cache sized for %lld rays, call has %lld", what,
                 (long long)o->sample_rays, (long long)P.ct.n_rays);
   const int64_t n = o->sample_rays, K = o->sample_cap;
@@ -714,6 +717,8 @@ extern "C" plx_status plx_render_batch(const plx_grid* g, const plx_cameras* cam
   P.ct.dense = 1;
   P.ct.n_rays = rows;
   P.ct.n_tiles = tiles;
+  st = set_sample_cache(what, opts, P, false);
+  if (st != PLX_OK) return st;
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);
   double* track_acc =
       reinterpret_cast<double*>(g->ws + sizeof(Workspace)) + (size_t)g->max_pose_blocks * 32;

@@ -10,7 +10,9 @@
 // involvement.
 //
 // Mapping tile: each lane marches its ray forward (C, D), forms the loss
-// gradient and marches again for the adjoint (as the separate kernels do).
+// gradient and marches again for the adjoint (as the separate kernels do);
+// with a sample cache the lane keeps its ray's compositing samples in its
+// own slot of it and the adjoint reads them back instead of re-marching.
 // Tracking tile: the per-ray Gauss-Newton contributions go through the warp
 // reduce-scatter; each lane keeps the FP64 sum of its value for the item it is
 // on and adds it into that item's FP64 accumulator when the warp moves to
@@ -82,7 +84,11 @@ k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
       sh_basis(r.dir, Y);
       float C[3], D, T;
       int n_all = 0, n_occ = 0;
-      march_forward<STORE, false>(P, r, Y, C, D, T, n_all, n_occ, 0);
+      // with a sample cache, thread slot `cslot` keeps this ray's compositing
+      // samples between its two marches (slots past the cache re-march)
+      const int64_t cslot = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+      const int cap = cslot < P.o.cn ? P.o.ccap : 0;
+      const int kept = march_forward<STORE, false>(P, r, Y, C, D, T, n_all, n_occ, cslot, cap);
       const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
       float gC[3], e2 = 0.f;
 #pragma unroll
@@ -93,7 +99,11 @@ k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
       }
       const float eD = D - Dt;
       mloss += (double)fmaf(P.o.lambda_d * eD, eD, e2);
-      march_backward<STORE>(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM, grad);
+      if (cap > 0 && kept <= cap)
+        march_backward_cached<false>(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM, grad,
+                                     cslot, kept);
+      else
+        march_backward<STORE>(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM, grad);
     }
   }
   if (slot >= 0) atomicAdd(track_acc + 32 * slot + lane, acc);

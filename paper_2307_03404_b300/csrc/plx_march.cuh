@@ -5,13 +5,13 @@
 
 namespace plx {
 
-// With the sample cache on (P.o.ccap > 0) the samples that composite are kept
-// for the grid adjoint: (sigma, colour) and k of the first ccap of them, and
-// their number, in row `out`.
+// With cap > 0 (the sample cache on) the samples that composite are kept for
+// the grid adjoint: (sigma, colour) and k of the first cap of them, and their
+// number, in row `out` of the cache; returns that number (0 when off).
 template <int STORE, bool COUNT>
-__device__ __forceinline__ void march_forward(const Common& P, const RayF& r, const float Y[9],
-                                              float C[3], float& D, float& T, int& n_all,
-                                              int& n_occ, int64_t out) {
+__device__ __forceinline__ int march_forward(const Common& P, const RayF& r, const float Y[9],
+                                             float C[3], float& D, float& T, int& n_all,
+                                             int& n_occ, int64_t out, int cap) {
   const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
   int cx = -1, cy = -1, cz = -1;
   bool empty = true;
@@ -56,8 +56,8 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
       float dact;
       col[ch] = activate(a, P.o.color_act, dact);
     }
-    if (P.o.ccap > 0) {
-      if (kept < P.o.ccap) {
+    if (cap > 0) {
+      if (kept < cap) {
         const int64_t at = (int64_t)kept * P.o.cn + out;
         P.o.cval[at] = make_float4(sig, col[0], col[1], col[2]);
         P.o.ck[at] = k;
@@ -77,9 +77,10 @@ __device__ __forceinline__ void march_forward(const Common& P, const RayF& r, co
       break;
     }
   }
-  if (P.o.ccap > 0) P.o.ccount[out] = kept;
+  if (cap > 0) P.o.ccount[out] = kept;
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], C[ch]);
+  return kept;
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -243,7 +244,10 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
 // cache (row `out`): sigma and colour are read back instead of interpolated,
 // so no cell record is gathered and no empty stretch is marched; only the
 // links of the cells holding those samples are loaded, for the scatter. The
-// per-sample arithmetic is march_backward's, in the same order.
+// per-sample arithmetic is march_backward's, in the same order. NC: read the
+// cache through the non-coherent path (it was written by an earlier launch;
+// not when the same thread has just written it in this one).
+template <bool NC>
 __device__ __forceinline__ void march_backward_cached(const Common& P, const RayF& r,
                                                       const float Y[9], const float Cf[3],
                                                       float Df, const float gC[3], float gD,
@@ -261,8 +265,8 @@ __device__ __forceinline__ void march_backward_cached(const Common& P, const Ray
   const bool ident = P.o.color_act == PLX_ACT_IDENTITY;
   for (int j = 0; j < n_kept; ++j) {
     const int64_t at = (int64_t)j * P.o.cn + out;
-    const float4 v = __ldg(P.o.cval + at);
-    const int k = __ldg(P.o.ck + at);
+    const float4 v = NC ? __ldg(P.o.cval + at) : P.o.cval[at];
+    const int k = NC ? __ldg(P.o.ck + at) : P.o.ck[at];
     const float kf = (float)k;
     int ix, iy, iz;
     float fx, fy, fz;

@@ -43,7 +43,7 @@ k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __re
   sh_basis(r.dir, Y);
   float C[3], D, T;
   int n_all = 0, n_occ = 0;
-  march_forward<STORE, COUNT>(P, r, Y, C, D, T, n_all, n_occ, id.out);
+  march_forward<STORE, COUNT>(P, r, Y, C, D, T, n_all, n_occ, id.out, P.o.ccap);
   rgb[3 * id.out] = C[0];
   rgb[3 * id.out + 1] = C[1];
   rgb[3 * id.out + 2] = C[2];
@@ -157,7 +157,7 @@ k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict
         if (n_kept <= P.o.ccap) {
           float Y[9];
           sh_basis(r.dir, Y);
-          march_backward_cached(P, r, Y, Cf, Df, gC, gD, grad, id.out, n_kept);
+          march_backward_cached<true>(P, r, Y, Cf, Df, gC, gD, grad, id.out, n_kept);
         }
       }
     }

@@ -355,6 +355,13 @@ class SampleCache:
         del probe
         return cls(n, cap)
 
+    @classmethod
+    def for_batch(cls, cap, device="cuda"):
+        """A cache for plx_render_batch: one row per thread slot of the
+        persistent launch (512 per SM), ``cap`` samples each."""
+        sms = torch.cuda.get_device_properties(torch.device(device)).multi_processor_count
+        return cls(512 * sms, cap, device=device)
+
     def opts(self, o):
         c = RenderOpts.from_buffer_copy(o)
         c.sample_cache = self.buf.data_ptr() if self.cap > 0 else None

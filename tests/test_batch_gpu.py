@@ -11,7 +11,11 @@ from paper_2307_03404_b300 import plx, scenes
 pytestmark = pytest.mark.gpu
 
 
-def test_batch_matches_separate_calls_and_oracle():
+@pytest.mark.parametrize("cache", [None, "all", "part"])
+def test_batch_matches_separate_calls_and_oracle(cache):
+    """cache "all": a sample cache row for every thread slot; "part": rows
+    for 100 slots only and 2 samples each, so most mapping rays re-march and
+    the rest overflow or fit."""
     g = scenes.tiny_grid(9, seed=41, alloc_frac=0.7, sigma_mean=2.0, sigma_std=2.0)
     T = [scenes.look_at((2.2, 1.4, -2.6), (0, 0.1, 0)), scenes.look_at((-2.0, 0.8, 2.4), (0.1, 0, 0)),
          scenes.look_at((2.6, -1.0, 1.5), (0, 0, 0))]
@@ -30,7 +34,12 @@ def test_batch_matches_separate_calls_and_oracle():
     o = plx.opts_from_dict(opts_d)
     grid = plx.Grid.from_scene(g, "f32")
     cams = plx.CameraSet(cams_np)
-    grad, mloss, H, b, tloss = plx.render_batch(grid, cams, work, o, dev(rgb_t), dev(depth_t))
+    ob = o
+    if cache == "all":
+        ob = plx.SampleCache.for_batch(64).opts(o)
+    elif cache == "part":
+        ob = plx.SampleCache(100, 2).opts(o)
+    grad, mloss, H, b, tloss = plx.render_batch(grid, cams, work, ob, dev(rgb_t), dev(depth_t))
     torch.cuda.synchronize()
     grid.check()
     offs = np.cumsum([0] + sizes)
