@@ -100,7 +100,7 @@ k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
       const float eD = D - Dt;
       mloss += (double)fmaf(P.o.lambda_d * eD, eD, e2);
       if (cap > 0 && kept <= cap)
-        march_backward_cached<false>(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM, grad,
+        march_backward_cached(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM, grad,
                                      cslot, kept);
       else
         march_backward<STORE>(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM, grad);

@@ -59,8 +59,10 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
     if (cap > 0) {
       if (kept < cap) {
         const int64_t at = (int64_t)kept * P.o.cn + out;
-        P.o.cval[at] = make_float4(sig, col[0], col[1], col[2]);
-        P.o.ck[at] = k;
+        // streaming stores: the cache is read once, by the next launch, and
+        // should not push the grid's lines out of L2
+        __stcs(P.o.cval + at, make_float4(sig, col[0], col[1], col[2]));
+        __stcs(P.o.ck + at, k);
       }
       ++kept;
     }
@@ -244,10 +246,9 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
 // cache (row `out`): sigma and colour are read back instead of interpolated,
 // so no cell record is gathered and no empty stretch is marched; only the
 // links of the cells holding those samples are loaded, for the scatter. The
-// per-sample arithmetic is march_backward's, in the same order. NC: read the
-// cache through the non-coherent path (it was written by an earlier launch;
-// not when the same thread has just written it in this one).
-template <bool NC>
+// per-sample arithmetic is march_backward's, in the same order. The cache is
+// read with coherent loads, so the batched launch may read back what the
+// same thread wrote earlier in it.
 __device__ __forceinline__ void march_backward_cached(const Common& P, const RayF& r,
                                                       const float Y[9], const float Cf[3],
                                                       float Df, const float gC[3], float gD,
@@ -265,8 +266,9 @@ __device__ __forceinline__ void march_backward_cached(const Common& P, const Ray
   const bool ident = P.o.color_act == PLX_ACT_IDENTITY;
   for (int j = 0; j < n_kept; ++j) {
     const int64_t at = (int64_t)j * P.o.cn + out;
-    const float4 v = NC ? __ldg(P.o.cval + at) : P.o.cval[at];
-    const int k = NC ? __ldg(P.o.ck + at) : P.o.ck[at];
+    // read once: evict-first, to keep the gradient rows in L2 for the atomics
+    const float4 v = __ldcs(P.o.cval + at);
+    const int k = __ldcs(P.o.ck + at);
     const float kf = (float)k;
     int ix, iy, iz;
     float fx, fy, fz;

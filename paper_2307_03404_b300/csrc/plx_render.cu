@@ -157,7 +157,7 @@ k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict
         if (n_kept <= P.o.ccap) {
           float Y[9];
           sh_basis(r.dir, Y);
-          march_backward_cached<true>(P, r, Y, Cf, Df, gC, gD, grad, id.out, n_kept);
+          march_backward_cached(P, r, Y, Cf, Df, gC, gD, grad, id.out, n_kept);
         }
       }
     }
