@@ -434,16 +434,19 @@ def run_ours(args):
     valid = np.isfinite(depth_np) & (depth_np > 0)
     hbm, peak_kind = peaks()
 
+    # the method's fixed no-reuse byte model (every pass gathers what it uses),
+    # and beside it the same model for the algorithm as run (with the sample
+    # cache the adjoint streams the kept samples instead of re-gathering)
     cap_main = main["cache"]["cap"] if main["cache"] else 0
-    fwd_b, bwd_b, s_all, s_occ = bytes_model(main["counts"], args.storage, valid, main["kept"],
-                                             cap_main)
+    fwd_b, bwd_b, s_all, s_occ = bytes_model(main["counts"], args.storage, valid)
+    fwd_i, bwd_i, _, _ = bytes_model(main["counts"], args.storage, valid, main["kept"], cap_main)
     fwd_ms, bwd_ms = statistics.mean(main["fwd_ms"]), statistics.mean(main["bwd_ms"])
     dom = "backward_grid" if bwd_ms >= fwd_ms else "forward"
     dom_b, dom_ms = (bwd_b, bwd_ms) if dom == "backward_grid" else (fwd_b, fwd_ms)
+    dom_i = bwd_i if dom == "backward_grid" else fwd_i
     achieved = dom_b / (dom_ms / 1e3) / 1e9
     step_roof = (fwd_b + bwd_b) / (hbm * 1e9) * 1e3   # ms per step at the HBM roof
-    fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage, valid, other["kept"],
-                                   other["cache"]["cap"] if other["cache"] else 0)
+    fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage, valid)
 
     # compulsory traffic of the adjoint: every touched vertex's record read
     # once, its FP32 gradient row read and written once, its link once
@@ -462,17 +465,22 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic,
-                     "model": "no-reuse byte model: 32 B of links per marched sample and pass, "
-                              "896 B (f32) / 448 B (16-bit) per gathered sample with an "
-                              "allocated corner, 32-36 B of per-ray I/O; with the sample "
-                              "cache the forward writes 20 B per compositing sample and the "
-                              "adjoint reads them back with 32 B of links and 1792 B of FP32 "
-                              "gradient RMW per such sample (rays that overflow the cache: "
-                              "32 B per marched sample, 896/448 + 1792 B per sample with an "
-                              "allocated corner); frac > 1 = beating the no-reuse bound "
-                              "through L1/L2 reuse",
+                     "model": "the method's fixed no-reuse byte model: 32 B of links per "
+                              "marched sample and pass, 896 B (f32) / 448 B (16-bit) per "
+                              "gathered sample with an allocated corner, in the adjoint again "
+                              "plus 1792 B of FP32 gradient RMW, 32-36 B of per-ray I/O; "
+                              "frac > 1 = beating the no-reuse bound through L1/L2 reuse",
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_per_launch": dom_b, "ms_per_launch": dom_ms,
+                     "as_run": {"bytes_per_launch": dom_i,
+                                "achieved": dom_i / (dom_ms / 1e3) / 1e9,
+                                "frac": dom_i / (dom_ms / 1e3) / 1e9 / hbm,
+                                "model": "the same model for the algorithm as run: with the "
+                                         "sample cache the forward also writes 20 B per "
+                                         "compositing sample and 4 B per ray, and the adjoint "
+                                         "of a ray that fits reads them back with 32 B of "
+                                         "links and 1792 B of gradient RMW per such sample "
+                                         "instead of re-marching"},
                      "step_frac": step_roof / (t_main / K),
                      "dram_gbs": dram_gbs if traffic else None,
                      "dram_frac": dram_gbs / hbm if traffic else None,
@@ -857,8 +865,9 @@ def run_large_bench(args, barrier):
     counts = plx.render_forward(grid, cams, o_plain, counts=True)["counts"].cpu().numpy()
     d = depth_t.cpu().numpy()
     valid = np.isfinite(d) & (d > 0)
-    fwd_b, bwd_b, s_all, s_occ = bytes_model(counts, storage, valid, kept,
-                                             cache_res["cap"] if cache_res else 0)
+    fwd_b, bwd_b, s_all, s_occ = bytes_model(counts, storage, valid)
+    _, bwd_i, _, _ = bytes_model(counts, storage, valid, kept,
+                                 cache_res["cap"] if cache_res else 0)
     hbm, peak_kind = peaks()
     achieved = bwd_b / (bwd_ms / 1e3) / 1e9
     touched = int((grad[:, :28] != 0).any(1).sum())
@@ -871,6 +880,8 @@ def run_large_bench(args, barrier):
            "roofline": {"bound": "hbm", "kernel": "backward_grid", "achieved": achieved,
                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_launch": bwd_b,
+                        "as_run": {"bytes_per_launch": bwd_i,
+                                   "frac": bwd_i / (bwd_ms / 1e3) / 1e9 / hbm},
                         "step_frac": (fwd_b + bwd_b) / (hbm * 1e9) * 1e3 / step_ms,
                         "S_all_mean": s_all, "S_occ_mean": s_occ,
                         "touched_vertices": touched,
