@@ -154,8 +154,9 @@ typedef struct {
  *   float [K][n][4]  (sigma, c_r, c_g, c_b) of kept sample j of ray r at [j][r]
  *   int32 [K][n]     its sample index k
  *   int32 [n]        the ray's number of samples with sigma > 0 (may exceed K)
- * in plx_sample_cache_bytes(n, K) bytes, owned by the caller; a call over more
- * than n rays fails with PLX_EINVAL. The adjoint
+ * in plx_sample_cache_bytes(n, K) bytes, owned by the caller, used by one
+ * call at a time (calls that share a cache must not run concurrently); a call
+ * over more than n rays fails with PLX_EINVAL. The adjoint
  * call must name the same cache and K, grid contents, cameras, rays and opts
  * as the forward that filled it (nothing checks this); without a cache it
  * re-marches every ray. Both ways give the same gradients up to the order of
