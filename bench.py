@@ -820,77 +820,90 @@ def run_large_bench(args, barrier):
     grid = plx.Grid.from_scene(sc.grid, storage)
     n_alloc = grid.n_alloc
     del sc
-    o_plain = o
-    scache = None
-    if args.sample_cache != "off":
-        scache = (plx.SampleCache.sized_for(grid, cams, o_plain) if args.sample_cache == "fit"
-                  else plx.SampleCache(n_rays, int(args.sample_cache)))
-        o = scache.opts(o_plain)
-    tuned = None
-    if not args.no_tune:
-        from paper_2307_03404_b300 import autotune
-
-        tuned = autotune.tune_mapping(grid, cams, o, rgb_t, depth_t, reps=1,
-                                      cache=os.path.join("/tmp", f"plx_tuning_{os.getpid()}.json"))
-    fw = plx.render_forward(grid, cams, o)
     grad = torch.zeros(n_alloc, plx.GRAD_STRIDE, device="cuda")
     loss = torch.empty(2, device="cuda", dtype=torch.float64)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def step(ev):
-        grad.zero_()
-        ev[0].record()
-        plx.render_forward(grid, cams, o, out=fw)
-        ev[1].record()
-        plx.render_backward_grid(grid, cams, o, rgb_t, depth_t, fw["rgb"], fw["depth"],
-                                 grad=grad, loss=loss)
-        ev[2].record()
-
+    tune_file = os.path.join("/tmp", f"plx_tuning_{os.getpid()}.json")
     K = max(2, args.steps // 2)
-    for _ in range(args.warmup):
-        step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
-    barrier()
-    E = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
-    for e in E:
-        flush.fill_(1)
-        step(e)
-    barrier()
-    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in E)
-    bwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in E)
+
+    def measure(oo):
+        """Autotune (unless off), then K timed forward + adjoint steps."""
+        tuned = None
+        if not args.no_tune:
+            from paper_2307_03404_b300 import autotune
+
+            tuned = autotune.tune_mapping(grid, cams, oo, rgb_t, depth_t, reps=1, cache=tune_file)
+        fw = plx.render_forward(grid, cams, oo)
+
+        def step(ev):
+            grad.zero_()
+            ev[0].record()
+            plx.render_forward(grid, cams, oo, out=fw)
+            ev[1].record()
+            plx.render_backward_grid(grid, cams, oo, rgb_t, depth_t, fw["rgb"], fw["depth"],
+                                     grad=grad, loss=loss)
+            ev[2].record()
+
+        for _ in range(args.warmup):
+            step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+        barrier()
+        E = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+        for e in E:
+            flush.fill_(1)
+            step(e)
+        barrier()
+        del fw
+        return (statistics.mean(e[0].elapsed_time(e[1]) for e in E),
+                statistics.mean(e[1].elapsed_time(e[2]) for e in E), tuned)
+
+    # the workload as defined: the adjoint recomputes every ray (only C, D and
+    # the final T are kept between the launches)
+    fwd_ms, bwd_ms, tuned = measure(o)
     step_ms = fwd_ms + bwd_ms
-    kept = scache.counts().cpu().numpy().copy() if scache is not None else None
-    cache_res = ({"cap": scache.cap, "bytes": plx.sample_cache_bytes(n_rays, scache.cap)}
-                 if scache is not None else None)
-    del scache
-    counts = plx.render_forward(grid, cams, o_plain, counts=True)["counts"].cpu().numpy()
+    loss_main = loss.cpu().tolist()
+    config_main = grid.get_config()
+    touched = int((grad[:, :28] != 0).any(1).sum())
+    counts = plx.render_forward(grid, cams, o, counts=True)["counts"].cpu().numpy()
     d = depth_t.cpu().numpy()
     valid = np.isfinite(d) & (d > 0)
     fwd_b, bwd_b, s_all, s_occ = bytes_model(counts, storage, valid)
-    _, bwd_i, _, _ = bytes_model(counts, storage, valid, kept,
-                                 cache_res["cap"] if cache_res else 0)
     hbm, peak_kind = peaks()
     achieved = bwd_b / (bwd_ms / 1e3) / 1e9
-    touched = int((grad[:, :28] != 0).any(1).sum())
     compulsory = touched * (64 + 2 * 112 + 4)
     out = {"workload": f"house1024: 1024^3 grid, {n_alloc} allocated "
                        f"({n_alloc / 1024 ** 3:.2%}), {storage} storage, 16 x 1200x680 keyframes "
-                       f"({n_rays} rays), step 0.5 voxel, <= 2048 samples per ray",
+                       f"({n_rays} rays), step 0.5 voxel, <= 2048 samples per ray; the adjoint "
+                       "recomputes each ray's state (no per-sample state kept)",
            "value": n_rays / (step_ms / 1e3), "unit": "rays/s", "ms_per_step": step_ms,
            "kernels_ms": {"forward": fwd_ms, "backward_grid": bwd_ms},
            "roofline": {"bound": "hbm", "kernel": "backward_grid", "achieved": achieved,
                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_launch": bwd_b,
-                        "as_run": {"bytes_per_launch": bwd_i,
-                                   "frac": bwd_i / (bwd_ms / 1e3) / 1e9 / hbm},
                         "step_frac": (fwd_b + bwd_b) / (hbm * 1e9) * 1e3 / step_ms,
                         "S_all_mean": s_all, "S_occ_mean": s_occ,
                         "touched_vertices": touched,
                         "compulsory_bytes_per_launch": compulsory,
                         "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9},
-           "loss": loss.cpu().tolist(), "launch_config": grid.get_config(),
-           "sample_cache": cache_note({"cache": cache_res, "kept": kept}, n_rays),
+           "loss": loss_main, "launch_config": config_main,
            "autotuned": tuned is not None, "steps": K,
            "scope": "one GPU (under torchrun every rank runs it; rank 0's numbers)"}
+    if args.sample_cache != "off":
+        # beside it, the same steps with the forward's compositing samples kept
+        # for the adjoint (tens of GB of per-sample state in HBM)
+        scache = (plx.SampleCache.sized_for(grid, cams, o) if args.sample_cache == "fit"
+                  else plx.SampleCache(n_rays, int(args.sample_cache)))
+        fc, bc, _ = measure(scache.opts(o))
+        kept = scache.counts().cpu().numpy().copy()
+        cache_res = {"cap": scache.cap, "bytes": plx.sample_cache_bytes(n_rays, scache.cap)}
+        del scache
+        _, bwd_i, _, _ = bytes_model(counts, storage, valid, kept, cache_res["cap"])
+        out["with_sample_cache"] = {
+            "value": n_rays / ((fc + bc) / 1e3), "unit": "rays/s", "ms_per_step": fc + bc,
+            "kernels_ms": {"forward": fc, "backward_grid": bc},
+            "sample_cache": cache_note({"cache": cache_res, "kept": kept}, n_rays),
+            "roofline_frac": bwd_b / (bc / 1e3) / 1e9 / hbm,
+            "as_run_frac": bwd_i / (bc / 1e3) / 1e9 / hbm,
+            "launch_config": grid.get_config()}
     grid.close()
     return out
 
