@@ -606,8 +606,26 @@ def run_tracking(args, world, rank, barrier):
         barrier()
         ms = [a.elapsed_time(b_) for a, b_ in evs]
         T = pose.cpu().numpy().reshape(3, 4)
+        ms_it = sum(ms) / len(ms) / iters
+        # the fixed no-reuse model of one iteration at the start pose (untimed):
+        # 32 B of links per marched sample, one gather per sample with an
+        # allocated corner, 16 B of targets per ray
+        pose_now = cams.poses.clone()
+        cams.poses.copy_(start)
+        cnt = plx.render_forward(grid, cams, o, counts=True)["counts"].cpu().numpy()
+        cams.poses.copy_(pose_now)
+        rec = 896.0 if storage == "f32" else 448.0
+        it_bytes = float((cnt[:, 0] * 32.0 + cnt[:, 1] * rec).sum() + 16.0 * cnt.shape[0])
+        hbm, peak_kind = peaks()
         res = {"value": iters * len(ms) / (sum(ms) / 1e3),
-               "ms_per_iter": sum(ms) / len(ms) / iters,
+               "ms_per_iter": ms_it,
+               "roofline": {"bound": "hbm", "bytes_per_iter": it_bytes,
+                            "achieved": it_bytes / (ms_it / 1e3) / 1e9, "peak": hbm,
+                            "unit": "GB/s", "frac": it_bytes / (ms_it / 1e3) / 1e9 / hbm,
+                            "peak_kind": f"{peak_kind} copy bandwidth",
+                            "model": "the method's fixed no-reuse model: per ray 32 B of links "
+                                     "per marched sample, 896 B (f32) / 448 B (16-bit) per "
+                                     "sample with an allocated corner, 16 B of targets"},
                "step": ("Gauss-Newton with Marquardt damping, accept/reject on the loss "
                         "(plx_pose_step_lm)" if method == "lm" else
                         "undamped Gauss-Newton (plx_pose_step)"),
@@ -669,6 +687,7 @@ def run_tracking(args, world, rank, barrier):
             "final_loss": float(buf[2][0].item())}
         grid.close()
     out["value"] = out["f32"]["value"]
+    out["roofline"] = out["f32"]["roofline"]
     return out
 
 
