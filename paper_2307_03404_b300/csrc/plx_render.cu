@@ -66,6 +66,43 @@ __global__ void k_count_valid(const float* __restrict__ depth_t, int64_t n,
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(M, local);
 }
 
+// A valid ray's RGB-D residual terms (Eq. 4, 5, 11): returns its squared
+// residual (loss before 1/M) and fills the forward's C, D and the loss
+// gradients dL/dC = 2 (C - C_t) / M, dL/dD = 2 lambda_d (D - D_t) / M.
+__device__ __forceinline__ float ray_residual(const Common& P, const RayF& r, int64_t out,
+                                              float dz, float invM,
+                                              const float* __restrict__ rgb_t,
+                                              const float* __restrict__ rgb,
+                                              const float* __restrict__ depth, float Cf[3],
+                                              float gC[3], float& Df, float& gD) {
+  const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
+  float e2 = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    Cf[ch] = __ldg(rgb + 3 * out + ch);
+    const float e = Cf[ch] - __ldg(rgb_t + 3 * out + ch);
+    e2 = fmaf(e, e, e2);
+    gC[ch] = 2.f * e * invM;
+  }
+  Df = __ldg(depth + out);
+  const float eD = Df - Dt;
+  gD = 2.f * P.o.lambda_d * eD * invM;
+  return fmaf(P.o.lambda_d * eD, eD, e2);
+}
+
+// Per warp: the FP64 sum of the lanes' squared residuals / M, one atomic per
+// warp; (L, M) in loss_out. All 32 lanes call it.
+__device__ __forceinline__ void add_warp_loss(float loss, double* __restrict__ loss_out,
+                                              const unsigned long long* __restrict__ Mc,
+                                              int lane) {
+  double s = (double)loss;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  const unsigned long long M = *Mc;
+  if (lane == 0 && s != 0.0) atomicAdd(loss_out, s / (double)M);
+  if (blockIdx.x == 0 && threadIdx.x == 0) loss_out[1] = (double)M;
+}
+
 template <int STORE, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB)
 k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
@@ -89,34 +126,14 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
       if (depth_valid(dz)) {
         float Y[9];
         sh_basis(r.dir, Y);
-        const float invM = (float)(1.0 / (double)M);
-        const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
-        float Cf[3], gC[3];
-        float e2 = 0.f;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          Cf[ch] = __ldg(rgb + 3 * id.out + ch);
-          const float e = Cf[ch] - __ldg(rgb_t + 3 * id.out + ch);
-          e2 = fmaf(e, e, e2);
-          gC[ch] = 2.f * e * invM;
-        }
-        const float Df = __ldg(depth + id.out);
-        const float eD = Df - Dt;
-        loss = fmaf(P.o.lambda_d * eD, eD, e2);
-        const float gD = 2.f * P.o.lambda_d * eD * invM;
+        float Cf[3], gC[3], Df, gD;
+        loss = ray_residual(P, r, id.out, dz, (float)(1.0 / (double)M), rgb_t, rgb, depth, Cf,
+                            gC, Df, gD);
         march_backward<STORE>(P, r, Y, Cf, Df, gC, gD, grad);
       }
     }
   }
-  if (loss_out) {
-    // per warp: FP64 sum of the rays' squared residuals, one atomic per warp
-    double s = (double)loss;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    const unsigned long long M = *Mc;
-    if (lane == 0 && s != 0.0) atomicAdd(loss_out, s / (double)M);
-    if (blockIdx.x == 0 && threadIdx.x == 0) loss_out[1] = (double)M;
-  }
+  if (loss_out) add_warp_loss(loss, loss_out, Mc, lane);
 }
 
 // The grid adjoint from the sample cache: every valid ray's loss term, and the
@@ -138,21 +155,9 @@ k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict
     if (id.valid && M > 0) {
       const float dz = __ldg(depth_t + id.out);
       if (depth_valid(dz)) {
-        const float invM = (float)(1.0 / (double)M);
-        const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
-        float Cf[3], gC[3];
-        float e2 = 0.f;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          Cf[ch] = __ldg(rgb + 3 * id.out + ch);
-          const float e = Cf[ch] - __ldg(rgb_t + 3 * id.out + ch);
-          e2 = fmaf(e, e, e2);
-          gC[ch] = 2.f * e * invM;
-        }
-        const float Df = __ldg(depth + id.out);
-        const float eD = Df - Dt;
-        loss = fmaf(P.o.lambda_d * eD, eD, e2);
-        const float gD = 2.f * P.o.lambda_d * eD * invM;
+        float Cf[3], gC[3], Df, gD;
+        loss = ray_residual(P, r, id.out, dz, (float)(1.0 / (double)M), rgb_t, rgb, depth, Cf,
+                            gC, Df, gD);
         const int n_kept = __ldg(P.o.ccount + id.out);
         if (n_kept <= P.o.ccap) {
           float Y[9];
@@ -162,14 +167,7 @@ k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict
       }
     }
   }
-  if (loss_out) {
-    double s = (double)loss;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    const unsigned long long M = *Mc;
-    if (lane == 0 && s != 0.0) atomicAdd(loss_out, s / (double)M);
-    if (blockIdx.x == 0 && threadIdx.x == 0) loss_out[1] = (double)M;
-  }
+  if (loss_out) add_warp_loss(loss, loss_out, Mc, lane);
 }
 
 // ------------------------------------------------------------ host launch
