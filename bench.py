@@ -698,6 +698,7 @@ def run_batch_bench(args, barrier):
 
     from paper_2307_03404_b300 import plx, scenes
 
+    torch.cuda.empty_cache()
     R, occ, npr, seed = scenes.WORKLOADS["room512mix"]
     t = time.time()
     sc = scenes.room_scene(R, occ, npr, seed)
@@ -824,6 +825,7 @@ def run_large_bench(args, barrier):
 
     from paper_2307_03404_b300 import plx, scenes
 
+    torch.cuda.empty_cache()  # what earlier legs left cached goes back to the device
     R, occ, npr, seed = scenes.WORKLOADS["house1024"]
     t = time.time()
     sc = scenes.house_scene(R, occ, npr, seed, device="cuda")
