@@ -370,6 +370,10 @@ class SampleCache:
         return c
 
     def counts(self):
+        """Compositing samples per ray (int32 [n_rays]) from the last forward
+        that filled this cache; only a cache with cap > 0 is ever filled."""
+        if self.cap == 0:
+            raise ValueError("a cache with cap 0 is never filled")
         off = 5 * self.cap * self.n_rays  # float4 [cap][n] then int32 [cap][n], in 4-byte words
         return self.buf[off:off + self.n_rays].view(torch.int32)
 
