@@ -5,7 +5,8 @@ empty-space map (blocks of 2^shift cells per axis) and, per ray kernel, the
 number of resident 256-thread blocks per SM it is compiled for (1 or 2: a
 register budget of 255 or 128 per thread). None of them changes a result; they
 trade occupancy against spills and skipping granularity against lookup cost,
-and the best values depend on the grid and the rays. The tuner times the
+and the best values depend on the grid and the rays, and on the options: with
+options naming a sample cache, tune_mapping times the cached adjoint. The tuner times the
 caller's own workload with CUDA events (coordinate descent, a few repetitions
 per candidate) and keeps the winner in a JSON cache keyed by device and
 workload, so later runs apply it without timing.
