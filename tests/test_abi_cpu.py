@@ -126,6 +126,27 @@ def test_sample_cache_size(lib):
     assert o.sample_cache is None and o.sample_cap == 0
 
 
+def test_sample_cache_binding_layout():
+    """The binding's view of a cache matches the header's layout: counts start
+    20 K n bytes in, and the options name the buffer, K and n (host buffer:
+    only the arithmetic is checked here)."""
+    import torch
+
+    from paper_2307_03404_b300 import plx
+
+    c = plx.SampleCache(10, 3, device="cpu")
+    assert c.buf.numel() * 4 == plx.sample_cache_bytes(10, 3)
+    cnt = c.counts()
+    assert cnt.dtype == torch.int32 and cnt.numel() == 10
+    assert cnt.data_ptr() - c.buf.data_ptr() == 20 * 3 * 10
+    o = c.opts(plx.make_opts(0.1))
+    assert o.sample_cache == c.buf.data_ptr() and o.sample_cap == 3 and o.sample_rays == 10
+    off = plx.SampleCache(10, 0, device="cpu")
+    assert off.opts(plx.make_opts(0.1)).sample_cache is None
+    with pytest.raises(ValueError):
+        off.counts()
+
+
 def test_grid_grow_argument_errors(lib):
     from paper_2307_03404_b300 import plx
 
