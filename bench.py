@@ -5,9 +5,12 @@ Workload (one step): every ray of 8 keyframes of 640x480 (2,457,600 rays)
 through a 256^3 grid with 10% of vertices allocated (analytic room with 20
 primitives): forward render (Eq. 1-3), RGB-D loss (Eq. 4, 5, 11) and its
 gradient to every grid value (Eq. 6-10), written into a zeroed gradient
-buffer. Tracking: 100 Gauss-Newton iterations (pose Jacobian + FP64 solve +
-SE(3) step) on one 640x480 frame against a 512^3 grid with 5% allocated,
-captured in one CUDA graph.
+buffer. By default the forward keeps each ray's compositing samples in a
+sample cache sized (untimed) by a probe forward, and the adjoint reads them
+back instead of re-marching (--sample-cache off re-marches every ray).
+Tracking: 100 Gauss-Newton iterations (pose Jacobian + FP64 solve + SE(3)
+step) on one 640x480 frame against a 512^3 grid with 5% allocated, captured
+in one CUDA graph.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank maps its own 8 keyframes of the same scene (weak
