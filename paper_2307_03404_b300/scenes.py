@@ -293,8 +293,36 @@ def _scene_sdf_grid(R, lo, hi, room_lo, room_hi, prims, margin_vox=12):
     return s, ids
 
 
+def _add_smooth_texture(sh, sel, R, h, amp, cell, rng, chunk=1 << 20):
+    """Adds to ``sh`` [n, 27] a smooth random field: N(0, amp) values on a
+    lattice of spacing ``cell`` covering the grid box, interpolated
+    trilinearly at the positions of the allocated vertices ``sel`` (flat
+    indices into the R^3 vertex lattice)."""
+    span = (R - 1) * h
+    m = np.ceil(span / cell).astype(int) + 2
+    lat = (amp * rng.standard_normal((m[2], m[1], m[0], sh.shape[1]))).astype(np.float32)
+    for a in range(0, sel.shape[0], chunk):
+        idx = sel[a:a + chunk]
+        iz, rem = np.divmod(idx, R * R)
+        iy, ix = np.divmod(rem, R)
+        q = [(ix * h[0]) / cell, (iy * h[1]) / cell, (iz * h[2]) / cell]
+        i0 = [np.minimum(np.floor(v).astype(np.int64), m[k] - 2) for k, v in enumerate(q)]
+        f = [(v - i0[k]).astype(np.float32)[:, None] for k, v in enumerate(q)]
+        acc = np.zeros((idx.shape[0], sh.shape[1]), np.float32)
+        for dz in (0, 1):
+            wz = f[2] if dz else 1 - f[2]
+            for dy in (0, 1):
+                wy = f[1] if dy else 1 - f[1]
+                for dx in (0, 1):
+                    wx = f[0] if dx else 1 - f[0]
+                    acc += (wx * wy * wz) * lat[i0[2] + dz, i0[1] + dy, i0[0] + dx]
+        sh[a:a + chunk] += acc
+
+
 def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 3.2,
-               wall_inset_vox: float = 4.0, border: int = 2) -> Scene:
+               wall_inset_vox: float = 4.0, border: int = 2, density_scale: float = 1.0,
+               vertex_noise: float = 0.1, smooth_texture: float = 0.0,
+               texture_cell: float = 0.1) -> Scene:
     """Analytic room: the six faces of a box inset by ``wall_inset_vox`` voxels
     from the grid box, plus ``n_prims`` random spheres and boxes. The vertices
     closest to the surfaces are allocated, as many as the fraction
@@ -305,6 +333,13 @@ def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 
     surface (wall or primitive) has its own N(0, 0.28) coefficients, and each
     vertex adds N(0, 0.1) to those of its nearest surface (about N(0, 0.3)
     overall): surfaces carry a colour with texture, as scanned rooms do.
+
+    Variants (defaults give the scene above): ``density_scale`` multiplies
+    every density (8 makes the surfaces opaque: a ray keeps about 1e-4 of its
+    transmittance after the room); ``vertex_noise`` is the per-vertex SH noise;
+    ``smooth_texture`` > 0 adds a spatially smooth texture of that standard
+    deviation: N(0, 1) values on a lattice of ``texture_cell`` metres, drawn
+    after everything else, interpolated trilinearly at each vertex.
     """
     rng = np.random.default_rng(seed)
     lo = np.full(3, -half)
@@ -335,10 +370,14 @@ def room_scene(R: int, occupancy: float, n_prims: int, seed: int, half: float = 
     w = max(float(np.abs(sv).max()), hm)
     density = ((0.6 / hm) * (0.5 - 0.6 * sv / w)
                + (0.05 / hm) * rng.standard_normal(n)).astype(np.float32)
+    if density_scale != 1.0:
+        density *= np.float32(density_scale)
     base = (0.28 * rng.standard_normal((6 + len(prims), N_SH))).astype(np.float32)
     sh = rng.standard_normal((n, N_SH), dtype=np.float32)
-    sh *= np.float32(0.1)
+    sh *= np.float32(vertex_noise)
     sh += base[surf]
+    if smooth_texture > 0.0:
+        _add_smooth_texture(sh, sel, R, h, smooth_texture, texture_cell, rng)
     grid = Grid((R, R, R), lo, hi, links, density, sh)
     return Scene(grid, prims, room_lo, room_hi)
 
@@ -733,3 +772,19 @@ WORKLOADS = {
     "room512mix": (512, 0.05, 20, 1004),
     "house1024": (1024, 0.02, 200, 1005),   # house_scene: multi-room, 12.8 m
 }
+
+# Scene variants per workload (room_scene keyword arguments). The tracking
+# workload's room is opaque with a texture that is smooth over 10 cm: on the
+# semi-transparent room (about 30% of each ray's transmittance is left after
+# the room, so expected depths blend several surfaces) and on per-vertex
+# white-noise texture (which decorrelates within one 1.25 cm voxel), the loss
+# over poses has minima other than the true pose within 3 cm of it.
+WORKLOAD_STYLE = {
+    "room512": dict(density_scale=8.0, vertex_noise=0.03, smooth_texture=0.2, texture_cell=0.1),
+}
+
+
+def workload_scene(name: str) -> Scene:
+    """The room scene of workload ``name`` (``WORKLOADS``, ``WORKLOAD_STYLE``)."""
+    R, occ, npr, seed = WORKLOADS[name]
+    return room_scene(R, occ, npr, seed, **WORKLOAD_STYLE.get(name, {}))

@@ -77,3 +77,11 @@ def rpe(est, gt, delta=1.0):
     t = np.linalg.norm(E[:, :3, 3], axis=1)
     r = rotation_angle_deg(E[:, :3, :3])
     return float(np.sqrt(np.mean(t * t))), float(np.sqrt(np.mean(r * r)))
+
+
+def pose_error(est, gt):
+    """(camera-centre distance in cm, rotation angle in degrees) between two
+    camera-to-world poses."""
+    e, g = _h(est), _h(gt)
+    d = 100.0 * float(np.linalg.norm(e[:3, 3] - g[:3, 3]))
+    return d, float(rotation_angle_deg(e[:3, :3] @ g[:3, :3].T))

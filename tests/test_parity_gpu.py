@@ -564,7 +564,7 @@ def test_room256_backward_sampled_and_partition(room256):
 @pytest.fixture(scope="module")
 def room512():
     R, occ, npr, seed = scenes.WORKLOADS["room512"]
-    sc = scenes.room_scene(R, occ, npr, seed)
+    sc = scenes.workload_scene("room512")
     cam = scenes.room_cameras(sc, 1, seed + 1)[0]
     rgb_t, depth_t = scenes.sensor_frames(sc, [cam], seed + 2)
     opts = dict(step=0.5 * sc.grid.h[0], lambda_d=1.0, depth_is_z=True)

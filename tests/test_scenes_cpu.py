@@ -47,3 +47,28 @@ def test_torch_sensor_model_matches_numpy(small_house):
     assert float(rgb_t.min()) >= 0.0 and float(rgb_t.max()) <= 1.0
     _, dz_m = scenes.sensor_frames_torch(small_house, cams, 1, device="cpu")
     assert 0.005 <= float((dz_m == 0).float().mean()) <= 0.04
+
+
+def test_room_variants_scale_density_and_add_a_smooth_texture():
+    """The tracking room's variant: the same links, densities scaled, and a
+    texture interpolated from a 10 cm lattice: strongly correlated between
+    neighbouring vertices (h = 6.7 cm here), unlike per-vertex noise."""
+    kw = dict(R=96, occupancy=0.1, n_prims=4, seed=21)
+    base = scenes.room_scene(**kw)
+    flat = scenes.room_scene(**kw, vertex_noise=0.0)
+    var = scenes.room_scene(**kw, density_scale=8.0, vertex_noise=0.0, smooth_texture=0.2,
+                            texture_cell=0.1)
+    np.testing.assert_array_equal(base.grid.links, var.grid.links)
+    np.testing.assert_allclose(var.grid.density, 8.0 * base.grid.density, rtol=1e-6)
+    tex = var.grid.sh - flat.grid.sh          # the smooth field alone
+    noise = base.grid.sh - flat.grid.sh       # the default per-vertex noise alone
+    lk = var.grid.links
+    a, b = lk[:, :, :-1].reshape(-1), lk[:, :, 1:].reshape(-1)
+    both = (a >= 0) & (b >= 0)
+
+    def corr(f):
+        x, y = f[a[both]].reshape(-1), f[b[both]].reshape(-1)
+        return float(np.corrcoef(x, y)[0, 1])
+
+    assert corr(tex) > 0.5 and abs(corr(noise)) < 0.05
+    assert 0.05 < float(tex.std()) < 0.2 and abs(float(noise.std()) - 0.1) < 0.005

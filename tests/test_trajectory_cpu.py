@@ -69,3 +69,22 @@ def test_rotation_drift_gives_known_relative_angle():
     assert t > 0.0
     assert trajectory.ate(e, g) < 1e-15
     assert abs(trajectory.rotation_angle_deg(rot_z(np.radians(37.0))) - 37.0) < 1e-9
+
+
+def test_pose_error_closed_form():
+    """A camera moved 3 cm and turned 2 degrees about any axis: (3, 2)."""
+    from scipy.spatial.transform import Rotation
+
+    from paper_2307_03404_b300.trajectory import pose_error
+
+    rng = np.random.default_rng(2)
+    T = np.zeros((3, 4))
+    T[:, :3] = Rotation.random(random_state=3).as_matrix()
+    T[:, 3] = rng.standard_normal(3)
+    u = rng.standard_normal(3)
+    u /= np.linalg.norm(u)
+    E = T.copy()
+    E[:, :3] = Rotation.from_rotvec(np.deg2rad(2.0) * u[::-1]).as_matrix() @ T[:, :3]
+    E[:, 3] += 0.03 * u
+    d_cm, d_deg = pose_error(E, T)
+    assert abs(d_cm - 3.0) < 1e-12 and abs(d_deg - 2.0) < 1e-9
