@@ -474,6 +474,29 @@ plx_status plx_render_batch(const plx_grid *grid, const plx_cameras *cams,
                             double *map_loss, double *JtWJ, double *JtWr,
                             double *track_loss, void *stream);
 
+/* Measurement kernels for the rooflines of the mapping kernels (the paper has
+ * none). The grid adjoint scatters each corner's 28 gradient values as 7
+ * float4 reductions into the vertex's 128-byte gradient row and the forward
+ * gathers 64- or 128-byte vertex records; both run mostly in L2, so their
+ * bound is the rate L2 sustains for such accesses, which these kernels issue
+ * with nothing else around them (time a launch with CUDA events):
+ *   PLX_PROBE_RED     each thread, `ops` times: a row drawn at random from
+ *                     n_rows (lanes in groups of `group` share it), 7 float4
+ *                     atomic adds of 1e-7 into its floats 0..27;
+ *                     7 * ops * threads reductions per launch
+ *   PLX_PROBE_GATHER  the same rows, 7 float4 loads each (read only)
+ *   PLX_PROBE_STREAM  `ops` coalesced float4 passes over all rows (read only)
+ *   buf     DEVICE float [n_rows][PLX_GRAD_STRIDE], 16-byte aligned, holding
+ *           finite values (RED adds to them); 1 <= n_rows < 2^32
+ *   blocks  thread blocks of 256 threads (1 .. 2^20); ops 1 .. 1024;
+ *           group 1 .. 32 (ignored by STREAM)
+ * Asynchronous. Errors: PLX_EINVAL, PLX_ECUDA. */
+#define PLX_PROBE_RED 0
+#define PLX_PROBE_GATHER 1
+#define PLX_PROBE_STREAM 2
+plx_status plx_probe(int32_t kind, float *buf, int64_t n_rows, int32_t group,
+                     int32_t ops, int32_t blocks, void *stream);
+
 /* Reads and clears the grid's device error word (synchronises `stream`).
  * Returns PLX_EDEVICE_CHECK if a device-side check failed since the last
  * call. */

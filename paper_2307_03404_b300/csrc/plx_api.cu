@@ -39,6 +39,8 @@ void launch_batch(int store, int minb, const Common& P, int n_track, const float
                   const float* depth_t, float* grad, double* map_loss, double* JtWJ, double* JtWr,
                   double* track_loss, unsigned long long* Mmap, double* track_acc,
                   unsigned long long* counter, int blocks, int num_sms, cudaStream_t s);
+void launch_probe(int kind, float* buf, uint32_t n_rows, int group, int ops, int blocks,
+                  cudaStream_t s);
 }  // namespace plx
 
 using namespace plx;
@@ -923,5 +925,23 @@ extern "C" plx_status plx_render_backward_pose_noalloc(
   launch_backward_pose(desc->storage, kDefaultPoseBlocks, P, rgb_target, depth_target,
                        reinterpret_cast<double*>(scratch + sizeof(Workspace)), &ws->retire, JtWJ,
                        JtWr, loss, max_blocks, s);
+  return launch_check(what);
+}
+
+// ------------------------------------------------------------ ceilings probe
+extern "C" plx_status plx_probe(int32_t kind, float* buf, int64_t n_rows, int32_t group,
+                                int32_t ops, int32_t blocks, void* stream) {
+  const char* what = "plx_probe";
+  if (kind != PLX_PROBE_RED && kind != PLX_PROBE_GATHER && kind != PLX_PROBE_STREAM)
+    return fail(PLX_EINVAL, "%s: unknown kind %d", what, kind);
+  if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15) != 0)
+    return fail(PLX_EINVAL, "%s: buffer null or not 16-byte aligned", what);
+  if (n_rows < 1 || n_rows > 0xffffffffll)
+    return fail(PLX_EINVAL, "%s: n_rows %lld out of [1, 2^32)", what, (long long)n_rows);
+  if (ops < 1 || ops > 1024 || blocks < 1 || blocks > (1 << 20))
+    return fail(PLX_EINVAL, "%s: ops %d or blocks %d out of range", what, ops, blocks);
+  if (kind != PLX_PROBE_STREAM && (group < 1 || group > 32))
+    return fail(PLX_EINVAL, "%s: group %d out of [1, 32]", what, group);
+  launch_probe(kind, buf, (uint32_t)n_rows, group, ops, blocks, (cudaStream_t)stream);
   return launch_check(what);
 }

@@ -1,0 +1,90 @@
+// Ceilings for the rooflines of the mapping kernels (no counterpart in the
+// paper). The grid adjoint is bound neither by DRAM bandwidth nor by the FP32
+// pipes: it scatters each corner's 28 gradient values as 7 float4 reductions
+// into the vertex's 128-byte gradient row, and those reductions run in L2.
+// The forward gathers 128-byte (FP32) or 64-byte (16-bit) records of
+// neighbouring vertices, mostly from L2. These kernels issue the same kinds of
+// accesses with nothing else around them, so a timed launch gives the rate
+// the memory system sustains for each:
+//   PLX_PROBE_RED     7 float4 reductions into one 128-byte row per lane and
+//                     operation, rows drawn at random from n_rows rows
+//                     (lanes in groups of `group` share a row: contention);
+//   PLX_PROBE_GATHER  7 float4 loads from one random row per lane and operation;
+//   PLX_PROBE_STREAM  coalesced float4 loads over all n_rows rows.
+// Every access stays inside [buf, buf + n_rows * 128 bytes): rows are drawn as
+// (hash * n_rows) >> 32 < n_rows and the stream walks indices below n_rows * 8.
+#include "plx_internal.cuh"
+
+namespace plx {
+
+__device__ __forceinline__ uint32_t probe_hash(uint32_t x) {
+  // integer finaliser (xorshift-multiply, the "lowbias32" constants)
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t probe_row(uint32_t key, uint32_t n_rows) {
+  return (uint32_t)(((uint64_t)probe_hash(key) * n_rows) >> 32);
+}
+
+__global__ void __launch_bounds__(256)
+k_probe_red(float* __restrict__ buf, uint32_t n_rows, int group, int ops) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t sub = lane / (uint32_t)group;
+  const float4 v = make_float4(1e-7f, 1e-7f, 1e-7f, 1e-7f);
+  for (int it = 0; it < ops; ++it) {
+    const uint32_t row = probe_row((warp * 1024u + (uint32_t)it) * 32u + sub, n_rows);
+    float4* dst = reinterpret_cast<float4*>(buf + (uint64_t)row * PLX_GRAD_STRIDE);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) atomicAdd(dst + j, v);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_probe_gather(float* __restrict__ buf, uint32_t n_rows, int group, int ops) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t sub = lane / (uint32_t)group;
+  float acc = 0.f;
+  for (int it = 0; it < ops; ++it) {
+    const uint32_t row = probe_row((warp * 1024u + (uint32_t)it) * 32u + sub, n_rows);
+    const float4* src = reinterpret_cast<const float4*>(buf + (uint64_t)row * PLX_GRAD_STRIDE);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const float4 q = __ldg(src + j);
+      acc += q.x + q.y + q.z + q.w;
+    }
+  }
+  // keeps the loads alive; the buffer holds finite values, so nothing is written
+  if (acc == -1.2345e38f) buf[0] = acc;
+}
+
+__global__ void __launch_bounds__(256)
+k_probe_stream(float* __restrict__ buf, uint32_t n_rows, int ops) {
+  const float4* src = reinterpret_cast<const float4*>(buf);
+  const uint64_t n4 = (uint64_t)n_rows * (PLX_GRAD_STRIDE / 4);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  float acc = 0.f;
+  for (int it = 0; it < ops; ++it)
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+      const float4 q = __ldcg(src + i);
+      acc += q.x + q.y + q.z + q.w;
+    }
+  if (acc == -1.2345e38f) buf[0] = acc;
+}
+
+void launch_probe(int kind, float* buf, uint32_t n_rows, int group, int ops, int blocks,
+                  cudaStream_t s) {
+  switch (kind) {
+    case PLX_PROBE_RED: k_probe_red<<<blocks, 256, 0, s>>>(buf, n_rows, group, ops); break;
+    case PLX_PROBE_GATHER: k_probe_gather<<<blocks, 256, 0, s>>>(buf, n_rows, group, ops); break;
+    default: k_probe_stream<<<blocks, 256, 0, s>>>(buf, n_rows, ops); break;
+  }
+}
+
+}  // namespace plx

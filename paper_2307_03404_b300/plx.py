@@ -83,7 +83,8 @@ SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload"
            "plx_render_backward_grid", "plx_render_backward_pose", "plx_pose_step",
            "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch",
            "plx_grid_rmsprop", "plx_track_adam_step", "plx_grid_get_config",
-           "plx_grid_set_config", "plx_grid_grow", "plx_pose_step_lm", "plx_sample_cache_bytes"]
+           "plx_grid_set_config", "plx_grid_grow", "plx_pose_step_lm", "plx_sample_cache_bytes",
+           "plx_probe"]
 
 
 def _load():
@@ -117,6 +118,7 @@ def _load():
                              P, P, P, P, P, P, P, P],
         "plx_pose_step_lm": [P, P, P, P, D, D, P, P, P, P],
         "plx_grid_grow": [C.POINTER(GridDesc), P, C.POINTER(Cameras), P, I32, D, P, P],
+        "plx_probe": [I32, P, I64, I32, I32, I32, P],
         "plx_render_backward_pose_noalloc": [C.POINTER(GridDesc), P, P, C.POINTER(Cameras), I32,
                                              C.POINTER(Rays), C.POINTER(RenderOpts), P, P, P, P,
                                              P, P],
@@ -545,3 +547,15 @@ def track_adam_step(grid: Grid, cams: CameraSet, cam: int, opts, n_rays, seed, r
                                     float(beta2), float(eps), _ptr(out[0]), _ptr(out[1]),
                                     _ptr(out[2]), _stream(stream)))
     return out
+
+
+PROBE_RED, PROBE_GATHER, PROBE_STREAM = 0, 1, 2
+
+
+def probe(kind, buf, group=1, ops=64, blocks=None, stream=None):
+    """plx_probe: one launch of a ceiling kernel over ``buf`` (float32
+    [n_rows, 32] on the device). ``blocks`` defaults to 8 per SM."""
+    if blocks is None:
+        blocks = 8 * torch.cuda.get_device_properties(buf.device).multi_processor_count
+    _check(_lib.plx_probe(int(kind), _ptr(buf), int(buf.shape[0]), int(group), int(ops),
+                          int(blocks), _stream(stream)))

@@ -213,3 +213,22 @@ def test_allocation_cap_reports_out_of_memory_before_allocating(lib):
                          cwd=ROOT, timeout=300)
     st, msg = out.stdout.strip().split(" ", 1)
     assert int(st) == 2 and "PLX_ALLOC_CAP_BYTES" in msg
+
+
+def test_probe_argument_errors(lib):
+    """plx_probe validates kind, buffer, sizes and group before any launch."""
+    from paper_2307_03404_b300 import plx
+
+    lib = plx._lib
+    fake = C.c_void_p(0x1000)  # never dereferenced: every call below fails its checks
+    assert lib.plx_probe(7, fake, 16, 1, 1, 1, None) == 1
+    assert b"kind" in lib.plx_last_error()
+    assert lib.plx_probe(0, None, 16, 1, 1, 1, None) == 1
+    assert lib.plx_probe(0, C.c_void_p(0x1004), 16, 1, 1, 1, None) == 1
+    assert b"aligned" in lib.plx_last_error()
+    assert lib.plx_probe(0, fake, 0, 1, 1, 1, None) == 1
+    assert b"n_rows" in lib.plx_last_error()
+    assert lib.plx_probe(1, fake, 16, 33, 1, 1, None) == 1
+    assert b"group" in lib.plx_last_error()
+    assert lib.plx_probe(2, fake, 16, 1, 0, 1, None) == 1
+    assert b"ops" in lib.plx_last_error()
