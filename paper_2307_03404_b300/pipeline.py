@@ -277,14 +277,19 @@ def track_sequence(grid: plx.Grid, cam_list, rgb_frames, depth_frames, opts, cfg
 
 
 def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", depth_noise=0.0025,
-        map_cfg=None, track_cfg=None, extra_track_cfgs=(), seed=21, log=None):
+        map_cfg=None, track_cfg=None, extra_track_cfgs=(), seed=21, log=None, map_last=True,
+        per_frame=False):
     """Whole pipeline on a synthetic room: a smooth sequence of ``n_frames``
     640x480 RGB-D frames along the first ``span`` of a spline path (depth
     noise N(0, (depth_noise z^2)^2), 2% of depths missing), every
     ``map_every``-th frame mapped with its true pose into a ``res``^3 dynamic
     grid over the scene's box, every frame tracked from the first true pose
     with ``track_cfg`` (and again with each of ``extra_track_cfgs``, on the
-    same map). Returns a dict of metrics and timings."""
+    same map). With ``map_last`` the last frame is a keyframe too, so that no
+    tracked frame looks past the mapped end of the sequence (without it the
+    frames after the last keyframe see space the map has never observed,
+    which renders empty, and tracking there drifts). ``per_frame`` adds each
+    frame's camera-centre error. Returns a dict of metrics and timings."""
     from . import scenes
 
     map_cfg = map_cfg or MapConfig()
@@ -300,6 +305,8 @@ def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", de
     opts = plx.opts_from_dict(dict(step=0.5 * float((g.hi[0] - g.lo[0]) / (R - 1)), lambda_d=1.0,
                                    depth_is_z=True))
     keys = list(range(0, n_frames, map_every))
+    if map_last and keys[-1] != n_frames - 1:
+        keys.append(n_frames - 1)
     kcams = plx.CameraSet([cams_np[k] for k in keys])
     krgb = rgb[keys].reshape(-1, 3).contiguous()
     kdepth = depth[keys].reshape(-1).contiguous()
@@ -318,9 +325,12 @@ def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", de
         err = np.linalg.norm(est[:, :, 3] - gt[:, :, 3], axis=1)
         desc = (f"Adam, {cfg.iters} iterations of {cfg.n_rays} random rays" if cfg.method == "adam"
                 else f"Levenberg-Marquardt, {cfg.lm_iters} whole-frame Jacobians")
-        return {"tracker": desc, "track_ms_per_frame": ms_frame,
-                "ate_m": trajectory.ate(est, gt), "rpe_t_m": t_rpe, "rpe_r_deg": r_rpe,
-                "median_err_m": float(np.median(err)), "max_err_m": float(err.max())}
+        res = {"tracker": desc, "track_ms_per_frame": ms_frame,
+               "ate_m": trajectory.ate(est, gt), "rpe_t_m": t_rpe, "rpe_r_deg": r_rpe,
+               "median_err_m": float(np.median(err)), "max_err_m": float(err.max())}
+        if per_frame:
+            res["err_m"] = err.tolist()
+        return res
 
     out = {"frames": n_frames, "keyframes": len(keys), "grid": f"{R}^3 dynamic, {storage}",
            "allocated": dg.n, "map_seconds": t_map, "map_steps": map_cfg.iters,
