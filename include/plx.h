@@ -222,16 +222,18 @@ plx_status plx_render_forward(const plx_grid *grid, const plx_cameras *cams,
  *   L = 1/M sum_valid |C - C_t|^2 + lambda_d/M sum_valid (D - D_t)^2
  * re-marches every valid ray (or, with a sample cache, visits the samples the
  * forward kept), recomputes T_i and the prefix sums of Eq. 9-10, and ADDS
- * dL/d(value) into `grad`.
+ * dL/d(value) into `grad`. With grad NULL only (L, M) is computed (no march,
+ * no sample cache read): the loss of a forward without its gradient.
  *   rgb_target   DEVICE float [n_rays][3]
  *   depth_target DEVICE float [n_rays] (see depth_is_z)
  *   rgb, depth   DEVICE float, the outputs of plx_render_forward for the
  *                same grid, cameras, rays and opts
  *   grad         DEVICE float [n_alloc][PLX_GRAD_STRIDE], 16-byte aligned:
  *                slot 0 = dL/d density, slots 1..27 = dL/d SH (canonical
- *                order), slots 28..31 untouched. The caller zeroes it.
+ *                order), slots 28..31 untouched. The caller zeroes it. NULL:
+ *                loss only.
  *   loss_out     DEVICE double [2] or NULL: overwritten with (L, M).
- * Errors: PLX_EINVAL, PLX_ECUDA. */
+ * Errors: PLX_EINVAL (also grad and loss_out both NULL), PLX_ECUDA. */
 plx_status plx_render_backward_grid(const plx_grid *grid,
                                     const plx_cameras *cams,
                                     const plx_rays *rays,

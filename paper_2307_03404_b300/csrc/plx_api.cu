@@ -579,8 +579,10 @@ plx_status plx_render_backward_grid(const plx_grid* g, const plx_cameras* cams,
   plx_status st = build_common("render_backward_grid", g, cams, rays, opts, -1, PLX_FINE_ADJOINT, P);
   if (st == PLX_OK) st = set_sample_cache("render_backward_grid", opts, P);
   if (st != PLX_OK) return st;
-  if (P.ct.n_rays > 0 && (!rgb_target || !depth_target || !rgb || !depth || !grad))
+  if (P.ct.n_rays > 0 && (!rgb_target || !depth_target || !rgb || !depth))
     return fail(PLX_EINVAL, "render_backward_grid: null array argument");
+  if (!grad && !loss_out)
+    return fail(PLX_EINVAL, "render_backward_grid: grad and loss_out both null");
   if (reinterpret_cast<uintptr_t>(grad) % 16 != 0)
     return fail(PLX_EINVAL, "render_backward_grid: grad must be 16-byte aligned");
   Workspace* ws = reinterpret_cast<Workspace*>(g->ws);

@@ -116,7 +116,10 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
   // hold, and a warp without such a ray leaves at once (the loss is then
   // summed by the cached launch, loss_out is null here)
   const RayId id = ray_of(P, tile < P.ct.n_tiles ? tile : 0, lane);
-  const bool todo = P.o.ccap == 0 || (id.valid && __ldg(P.o.ccount + id.out) > P.o.ccap);
+  // grad null: the loss of every valid ray and nothing else
+  const bool loss_only = grad == nullptr;
+  const bool todo = loss_only || P.o.ccap == 0 ||
+                    (id.valid && __ldg(P.o.ccount + id.out) > P.o.ccap);
   if (tile < P.ct.n_tiles && __any_sync(0xffffffffu, todo)) {
     RayF r;
     setup_ray(P, id, r, lane);
@@ -129,7 +132,7 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
         float Cf[3], gC[3], Df, gD;
         loss = ray_residual(P, r, id.out, dz, (float)(1.0 / (double)M), rgb_t, rgb, depth, Cf,
                             gC, Df, gD);
-        march_backward<STORE>(P, r, Y, Cf, Df, gC, gD, grad);
+        if (!loss_only) march_backward<STORE>(P, r, Y, Cf, Df, gC, gD, grad);
       }
     }
   }
@@ -197,7 +200,7 @@ void launch_backward_grid(int store, int minb, const Common& P, const float* rgb
   if (P.ct.n_tiles == 0) return;
   const unsigned blocks = (unsigned)((P.ct.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
   double* loss_full = loss_out;
-  if (P.o.ccap > 0) {  // the cache's rays (and every loss term), then the overflow
+  if (P.o.ccap > 0 && grad) {  // the cache's rays (and every loss term), then the overflow
     if (minb == 1)
       k_backward_grid_cached<1><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad,
                                                           loss_out, M);
