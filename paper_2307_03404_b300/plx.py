@@ -213,6 +213,7 @@ class Grid:
     def upload(self, density, sh, stream=None):
         _check(_lib.plx_grid_upload(self._h, _ptr(density.contiguous()),
                                     _ptr(sh.contiguous()), _stream(stream)))
+        self._autograd_values = None  # autograd.mapping_loss uploads again
 
     def download(self, stream=None):
         density = torch.empty(self.n_alloc, device="cuda")
@@ -232,6 +233,9 @@ class Grid:
         """Change launch choices (block_shift, fine_skip, forward_blocks,
         adjoint_blocks, pose_blocks, batch_blocks); results do not change."""
         cur = self.get_config()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown launch choices {sorted(unknown)}")
         cur.update({k: int(v) for k, v in kw.items()})
         c = LaunchConfig(**cur)
         _check(_lib.plx_grid_set_config(self._h, C.byref(c), _stream(stream)))
@@ -365,10 +369,14 @@ class SampleCache:
         return cls(512 * sms, cap, device=device)
 
     def opts(self, o):
+        """A copy of the options ``o`` naming this cache. The copy holds a
+        reference to the cache, so its device memory lives as long as options
+        that point at it (a temporary SampleCache(...).opts(o) stays valid)."""
         c = RenderOpts.from_buffer_copy(o)
         c.sample_cache = self.buf.data_ptr() if self.cap > 0 else None
         c.sample_cap = self.cap
         c.sample_rays = self.n_rays
+        c._cache = self
         return c
 
     def counts(self):
@@ -410,9 +418,12 @@ def render_forward(grid: Grid, cams: CameraSet, opts, rays=None, state=True, cou
 def render_backward_grid(grid: Grid, cams: CameraSet, opts, rgb_target, depth_target, rgb,
                          depth, rays=None, grad=None, loss=None, stream=None):
     """plx_render_backward_grid. Adds into ``grad`` [n_alloc, 32] (allocated
-    zeroed when None); returns (grad, loss [2] float64 = (L, M))."""
+    zeroed when None; ``grad=False``: loss only, returned grad None); returns
+    (grad, loss [2] float64 = (L, M))."""
     r, keep = make_rays(*(rays if rays is not None else (None, None)))
-    if grad is None:
+    if grad is False:
+        grad = None
+    elif grad is None:
         grad = torch.zeros(grid.n_alloc, GRAD_STRIDE, device="cuda")
     if loss is None:
         loss = torch.empty(2, device="cuda", dtype=torch.float64)
@@ -500,6 +511,7 @@ def grid_rmsprop(grid: Grid, grad, state, lr, alpha=0.99, eps=1e-8, zero_grad=Tr
     (``lr`` for the SH values, ``lr_density`` for the density; the same if
     not given)."""
     lr_d = lr if lr_density is None else lr_density
+    grid._autograd_values = None  # the stored values change
     _check(_lib.plx_grid_rmsprop(grid.handle, _ptr(grad), _ptr(state), float(lr_d), float(lr),
                                  float(alpha), float(eps), int(bool(zero_grad)), _stream(stream)))
 

@@ -232,3 +232,22 @@ def test_probe_argument_errors(lib):
     assert b"group" in lib.plx_last_error()
     assert lib.plx_probe(2, fake, 16, 1, 0, 1, None) == 1
     assert b"ops" in lib.plx_last_error()
+
+
+def test_sample_cache_options_keep_the_cache_alive():
+    """Options made by SampleCache.opts hold the cache: a temporary cache's
+    device buffer is not freed (and reused) while the options live."""
+    import gc
+    import weakref
+
+    from paper_2307_03404_b300 import plx
+
+    cache = plx.SampleCache(4, 2, device="cpu")
+    ref = weakref.ref(cache)
+    o = cache.opts(plx.make_opts(0.1))
+    del cache
+    gc.collect()
+    assert ref() is not None and o.sample_cap == 2
+    del o
+    gc.collect()
+    assert ref() is None
