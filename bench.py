@@ -68,6 +68,7 @@ def combine_rank_times(times_ms, units_per_rank):
 KERNEL_SOURCES = {
     "forward": ("plx_internal.cuh", "plx_march.cuh", "plx_render.cu"),
     "backward_grid": ("plx_internal.cuh", "plx_march.cuh", "plx_render.cu"),
+    "backward_pose": ("plx_internal.cuh", "plx_pose_march.cuh", "plx_pose.cu"),
 }
 
 
@@ -111,12 +112,15 @@ def _per_launch(rec, key, n_rays):
     return v
 
 
-def measured_traffic(kernel, workload, storage, n_rays=None):
+def measured_traffic(kernel, workload, storage, n_rays=None, key="dram_bytes_per_launch"):
+    """An ncu per-launch figure of profiles/traffic.json (DRAM bytes by
+    default; ``key`` names another, e.g. red_requests_per_launch), scaled to
+    n_rays rays; None if no record was taken on the current sources."""
     rec = measured_profile(kernel, workload, storage)
-    return _per_launch(rec, "dram_bytes_per_launch", n_rays) if rec else None
+    return _per_launch(rec, key, n_rays) if rec and key in rec else None
 
 
-def issue_roofline(kernel, ms, storage, clocks, n_rays=None):
+def issue_roofline(kernel, ms, storage, clocks, n_rays=None, workload="room256"):
     """Instruction-issue utilisation of a kernel: warp instructions per launch
     (ncu, profiles/traffic.json, valid for the current sources, scaled to
     n_rays rays) over the live launch time, against one warp instruction per
@@ -124,7 +128,7 @@ def issue_roofline(kernel, ms, storage, clocks, n_rays=None):
     run."""
     import torch
 
-    rec = measured_profile(kernel, "room256", storage)
+    rec = measured_profile(kernel, workload, storage)
     if not rec or "warp_instructions_per_launch" not in rec:
         return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -135,6 +139,115 @@ def issue_roofline(kernel, ms, storage, clocks, n_rays=None):
     return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s",
             "frac": achieved / peak, "warp_instructions_per_launch": wi,
             "peak_basis": f"{sms} SMs x 4 sub-partitions x 1 warp instruction per clock x {mhz:.0f} MHz"}
+
+
+def l2_ceilings(rows=600_000, reps=5):
+    """Rates the memory system sustains for the mapping kernels' L2 accesses,
+    measured live with the library's probe kernels (plx_probe) over a buffer of
+    ``rows`` 128-byte rows (the size of the set of vertices one room256 step
+    touches, so it stays in L2): float4 reductions into random rows (7 per row,
+    as the adjoint's corner flush) and float4 gathers of random rows (as the
+    record gathers). Best of 8 and 16 blocks of 256 threads per SM."""
+    import torch
+
+    from paper_2307_03404_b300 import plx
+
+    buf = torch.zeros(rows, plx.GRAD_STRIDE, device="cuda")
+    sms = torch.cuda.get_device_properties(buf.device).multi_processor_count
+    out = {}
+    for kind, name in ((plx.PROBE_RED, "red"), (plx.PROBE_GATHER, "gather")):
+        best = 0.0
+        for bps in (8, 16):
+            blocks, ops = bps * sms, 32
+            for _ in range(2):
+                plx.probe(kind, buf, 1, ops, blocks)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                plx.probe(kind, buf, 1, ops, blocks)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            best = max(best, blocks * 256 * ops * 7 / (ms / 1e3))
+        out[name] = best
+    del buf
+    return {"red_per_s": out["red"], "gather_float4_per_s": out["gather"],
+            "buffer_MB": rows * 128 / 1e6,
+            "how": "plx_probe: each lane 32 times picks a random 128-byte row of the buffer and "
+                   "issues 7 float4 atomic adds (red) or 7 float4 loads (gather) to it; best of "
+                   "8 and 16 blocks of 256 threads per SM, CUDA events over 5 launches"}
+
+
+def l2_roofline(kernel, workload, storage, n_rays, ms, ceil):
+    """The L2 rates of a kernel against the probe ceilings: reduction requests
+    (lts__t_requests_srcunit_tex_op_red.sum) and read requests
+    (lts__t_requests_srcunit_tex_op_read.sum) per launch from the ncu record
+    of profiles/traffic.json (taken on the current sources, scaled to n_rays
+    rays) over the launch time measured here. None where no record matches."""
+    out = {}
+    for key, name, peak in (("red_requests_per_launch", "red", ceil["red_per_s"]),
+                            ("read_requests_per_launch", "read", ceil["gather_float4_per_s"])):
+        n = measured_traffic(kernel, workload, storage, n_rays, key=key)
+        if n:
+            rate = n / (ms / 1e3)
+            out[name] = {"per_launch": n, "achieved": rate, "peak": peak, "frac": rate / peak,
+                         "unit": "requests/s"}
+    return out or None
+
+
+def roofline_block(kernel, workload, storage, n_rays, ms, ceil, compulsory, no_reuse_bytes,
+                   hbm_model, clocks=None):
+    """The roofline object of a dominant kernel. When its ncu record exists
+    the binding ceiling is whichever the kernel comes closest to: the L2
+    reduction rate (the grid adjoint's scatter), the L2 gather rate (record
+    gathers) or instruction issue (bound "alu": one warp instruction per
+    clock per SM sub-partition); the HBM figure beside it uses the compulsory
+    bytes (what the kernel cannot avoid moving), and the survey's no-reuse
+    model stays only as a diagnostic."""
+    hbm, peak_kind = peaks()
+    comp_gbs = compulsory / (ms / 1e3) / 1e9
+    traffic = measured_traffic(kernel, workload, storage, n_rays)
+    dram_gbs = traffic / (ms / 1e3) / 1e9 if traffic else None
+    l2 = l2_roofline(kernel, workload, storage, n_rays, ms, ceil)
+    block = {"kernel": kernel, "ms_per_launch": ms, "traffic": traffic}
+    hb = {"achieved": comp_gbs, "peak": hbm, "unit": "GB/s", "frac": comp_gbs / hbm,
+          "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_launch": compulsory,
+          "model": hbm_model, "dram_gbs": dram_gbs,
+          "dram_frac": dram_gbs / hbm if dram_gbs else None}
+    nr = no_reuse_bytes / (ms / 1e3) / 1e9
+    block["no_reuse"] = {
+        "bytes_per_launch": no_reuse_bytes, "achieved": nr, "peak": hbm, "frac": nr / hbm,
+        "model": "a diagnostic, not a roofline: the survey's fixed no-reuse byte model (32 B of "
+                 "links per marched sample, 896 B (f32) / 448 B (16-bit) per sample with an "
+                 "allocated corner per gather, 1792 B of FP32 gradient read-modify-write per "
+                 "such sample in the adjoint, per-ray I/O); frac > 1 means L1/L2 reuse, not HBM "
+                 "use"}
+    issue = issue_roofline(kernel, ms, storage, clocks, n_rays, workload)
+    cands = dict(l2 or {})
+    if issue:
+        cands["issue"] = issue
+    if cands:
+        name = max(cands, key=lambda k: cands[k]["frac"])
+        b = cands[name]
+        block.update({"bound": {"red": "l2_atomic", "read": "l2_gather", "issue": "alu"}[name],
+                      "achieved": b["achieved"], "peak": b["peak"], "unit": b["unit"],
+                      "frac": b["frac"], "l2": l2, "issue": issue, "hbm": hb,
+                      "basis": "the kernel moves little DRAM traffic (hbm below). Per ncu "
+                               "record (profiles/traffic.json, taken on the current sources, "
+                               "scaled by rays) over the launch time measured here: L2 "
+                               "reduction / read requests against the rate plx_probe measures "
+                               "live for the same access (float4 reductions or gathers of "
+                               "random 128-byte rows in L2), and warp instructions against "
+                               "one per clock per SM sub-partition at the sampled clock "
+                               "(alu); bound = the largest of these fractions"})
+    else:
+        block.update({"bound": "hbm", "achieved": comp_gbs, "peak": hbm, "unit": "GB/s",
+                      "frac": comp_gbs / hbm, "hbm": hb,
+                      "basis": "no ncu record of this kernel's L2 requests on the current "
+                               "sources: the HBM roofline of its compulsory bytes"})
+    block["ceilings"] = ceil
+    return block
 
 
 def peaks():
@@ -292,17 +405,18 @@ def run_ours(args):
 
     tune_cache = os.path.join("/tmp", f"plx_tuning_{os.getpid()}.json")
 
-    def measure(storage, K, W, with_e2e):
+    def measure(storage, K, W, with_e2e, cache_mode=None):
         grid = plx.Grid.from_scene(sc.grid, storage)
         # sample cache: forward keeps each ray's compositing samples for the
         # adjoint; sized (untimed) by a probe forward so that no ray overflows
         scache = None
         o = o_plain
-        if args.sample_cache != "off":
-            if args.sample_cache == "fit":
+        cache_mode = cache_mode or args.sample_cache
+        if cache_mode != "off":
+            if cache_mode == "fit":
                 scache = plx.SampleCache.sized_for(grid, cams, o_plain)
             else:
-                scache = plx.SampleCache(n_rays, int(args.sample_cache))
+                scache = plx.SampleCache(n_rays, int(cache_mode))
             o = scache.opts(o_plain)
         tuned = None
         if not args.no_tune:
@@ -424,6 +538,10 @@ def run_ours(args):
         main = measure(args.storage, K, W, with_e2e=True)
         other_storage = "bf16" if args.storage == "f32" else "f32"
         other = measure(other_storage, K, W, with_e2e=False)
+        # the workload's other form: the adjoint recomputes every ray (no
+        # per-sample state kept between the passes)
+        recomp = (measure(args.storage, K, W, with_e2e=False, cache_mode="off")
+                  if main["cache"] else None)
     clocks = clk.summary()
 
     # whole-job numbers: max over ranks
@@ -451,13 +569,38 @@ def run_ours(args):
     step_roof = (fwd_b + bwd_b) / (hbm * 1e9) * 1e3   # ms per step at the HBM roof
     fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage, valid)
 
-    # compulsory traffic of the adjoint: every touched vertex's record read
-    # once, its FP32 gradient row read and written once, its link once
+    # compulsory traffic of the dominant kernel, the bytes it cannot avoid:
+    # every touched vertex's FP32 gradient row (28 values) read and written
+    # once and its link read once; without a sample cache also its record
+    # read once; with one, the kept samples (20 B each) and the per-ray counts
+    # read once; per valid ray its targets and the forward's C and D
     rec_b = 128 if args.storage == "f32" else 64
-    compulsory = main["touched"] * (rec_b + 2 * 112 + 4)
-    traffic = measured_traffic(dom, "room256", args.storage, n_rays)
-    if traffic:
-        dram_gbs = traffic / (dom_ms / 1e3) / 1e9
+    n_valid = int(valid.sum())
+    kept_fit = 0.0
+    if main["kept"] is not None:
+        k = main["kept"].astype(np.float64)
+        kept_fit = float(k[valid & (main["kept"] <= cap_main)].sum())
+    compulsory = (main["touched"] * (2 * 112 + 4) + 32.0 * n_valid
+                  + (kept_fit * 20.0 + 4.0 * n_rays if main["cache"] else main["touched"] * rec_b))
+    ceil = l2_ceilings()
+    roofline = roofline_block(
+        dom, "room256", args.storage, n_rays, dom_ms, ceil, compulsory, dom_b,
+        "compulsory bytes: per touched vertex 2 x 112 B of FP32 gradient read-modify-write "
+        "and 4 B of link; with the sample cache 20 B per kept sample and 4 B per ray, without "
+        "it the vertex record once; 32 B per valid ray (targets, forward's C and D)", clocks)
+    fwd_comp = main["touched"] * (rec_b + 4) + 20.0 * kept_fit + 20.0 * n_rays
+    fwd_block = roofline_block(
+        "forward", "room256", args.storage, n_rays, fwd_ms, ceil, fwd_comp, fwd_b,
+        "compulsory bytes: per touched vertex its record and link once; with the sample "
+        "cache 20 B per kept sample written; 20 B of outputs per ray", clocks)
+    roofline.update({
+        "as_run_no_reuse_frac": dom_i / (dom_ms / 1e3) / 1e9 / hbm,
+        "step_no_reuse_frac": step_roof / (t_main / K),
+        "S_all_mean": s_all, "S_occ_mean": s_occ, "touched_vertices": main["touched"],
+        "forward": {k: fwd_block[k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                              "ms_per_launch", "traffic", "l2", "issue", "hbm")
+                    if k in fwd_block},
+    })
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": t_main / K, "higher_is_better": True, "scaling": "weak",
@@ -465,33 +608,7 @@ def run_ours(args):
         "config": dict(workload_config(sc, cams_np, args.storage),
                        parallelism=f"replicated grid, keyframes sharded over {world} rank(s)",
                        sample_cache=cache_note(main, n_rays)),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic,
-                     "model": "the method's fixed no-reuse byte model: 32 B of links per "
-                              "marched sample and pass, 896 B (f32) / 448 B (16-bit) per "
-                              "gathered sample with an allocated corner, in the adjoint again "
-                              "plus 1792 B of FP32 gradient RMW, 32-36 B of per-ray I/O; "
-                              "frac > 1 = beating the no-reuse bound through L1/L2 reuse",
-                     "peak_kind": f"{peak_kind} copy bandwidth",
-                     "bytes_per_launch": dom_b, "ms_per_launch": dom_ms,
-                     "as_run": {"bytes_per_launch": dom_i,
-                                "achieved": dom_i / (dom_ms / 1e3) / 1e9,
-                                "frac": dom_i / (dom_ms / 1e3) / 1e9 / hbm,
-                                "model": "the same model for the algorithm as run: with the "
-                                         "sample cache the forward also writes 20 B per "
-                                         "compositing sample and 4 B per ray, and the adjoint "
-                                         "of a ray that fits reads them back with 32 B of "
-                                         "links and 1792 B of gradient RMW per such sample "
-                                         "instead of re-marching"},
-                     "step_frac": step_roof / (t_main / K),
-                     "dram_gbs": dram_gbs if traffic else None,
-                     "dram_frac": dram_gbs / hbm if traffic else None,
-                     "S_all_mean": s_all, "S_occ_mean": s_occ,
-                     "touched_vertices": main["touched"],
-                     "compulsory_bytes_per_launch": compulsory,
-                     "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9,
-                     "issue": issue_roofline(dom, dom_ms, args.storage, clocks, n_rays)},
+        "roofline": roofline,
         "e2e": {"value": rays_job / (t_e2e / 1e3), "unit": "rays/s",
                 "h2d_bytes_per_step": main["h2d"], "d2h_bytes_per_step": main["d2h"],
                 "timing": "K steps as one region (first copy to last loss read); copies of "
@@ -502,6 +619,15 @@ def run_ours(args):
         other_storage: {"value": rays_job / (t_other / 1e3), "unit": "rays/s",
                         "ms_per_step": t_other / K,
                         "step_frac": (fo_b + bo_b) / (hbm * 1e9) * 1e3 / (t_other / K)},
+        "recompute": None if recomp is None else {
+            "value": rays_job / (rank_max(sum(recomp["step_ms"]), world, "cuda") / 1e3),
+            "unit": "rays/s", "storage": args.storage,
+            "ms_per_step": rank_max(sum(recomp["step_ms"]), world, "cuda") / K,
+            "kernels_ms": {"forward": statistics.mean(recomp["fwd_ms"]),
+                           "backward_grid": statistics.mean(recomp["bwd_ms"])},
+            "note": "the same step without the sample cache: the adjoint re-marches every ray, "
+                    "recomputing T_i and the prefix sums; the headline keeps "
+                    f"{main['cache']['bytes'] / 1e9:.2f} GB of kept samples instead"},
         "loss": main["loss"],
         "kernels_ms": {"forward": fwd_ms, "backward_grid": bwd_ms},
         "launch_config": {"autotuned": not args.no_tune, args.storage: main["launch_config"],
@@ -509,8 +635,10 @@ def run_ours(args):
         "tuning_trials": main["tuning_trials"],
         "kernel_source_sha": kernel_source_sha(),
     }
+    if not args.no_small:
+        line["small"] = run_small_bench(args, barrier)
     if not args.no_tracking:
-        line["tracking"] = run_tracking(args, world, rank, barrier)
+        line["tracking"] = run_tracking(args, world, rank, barrier, clocks)
     if not args.no_batch:
         line["batched"] = run_batch_bench(args, barrier)
     if not args.no_large:
@@ -525,7 +653,7 @@ def run_ours(args):
         pl = pipeline.run(sc, log=log,
                           extra_track_cfgs=[pipeline.TrackConfig(method="lm", lm_iters=10)])
         pl["wall_seconds"] = time.time() - t
-        pl["workload"] = ("room256 geometry, 300-frame 640x480 sequence (path_m long), every 10th "
+        pl["workload"] = ("room256 geometry, 300-frame 640x480 sequence (path_m long), every 10th and the last "
                           "frame mapped into a dynamic 256^3 grid grown from depth, every frame "
                           "tracked (Adam, 200 iterations of 4096 random rays, one CUDA graph; again with "
                           "10 Levenberg-Marquardt iterations on whole frames)")
@@ -539,15 +667,17 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_tracking(args, world, rank, barrier):
-    """Tracking iterations/s: 100 GN iterations in one CUDA graph."""
+def run_tracking(args, world, rank, barrier, clk=None):
+    """Tracking iterations/s: 100 GN iterations in one CUDA graph (``clk``:
+    the clocks sampled during the mapping leg, for the issue roofline)."""
     import torch
 
     from paper_2307_03404_b300 import plx, scenes
+    from paper_2307_03404_b300.trajectory import pose_error
 
     R, occ, npr, seed = scenes.WORKLOADS[args.tracking_workload]
     t = time.time()
-    sc = scenes.room_scene(R, occ, npr, seed)
+    sc = scenes.workload_scene(args.tracking_workload)
     cam = scenes.room_cameras(sc, 1, seed + 1 + rank)[0]
     log(f"[bench] {args.tracking_workload} tracking scene in {time.time() - t:.1f}s")
     opts = dict(step=0.5 * float(sc.grid.h[0]), lambda_d=1.0, depth_is_z=False)
@@ -555,9 +685,11 @@ def run_tracking(args, world, rank, barrier):
     T0 = scenes.perturb_pose(cam.T_wc, 0.03, 2.0, np.random.default_rng(seed + 5))
     iters = args.tracking_iters
     out = {"workload": f"{args.tracking_workload}: {R}^3 grid, {sc.grid.n_alloc} allocated, "
-                       f"one 640x480 frame, {iters} Gauss-Newton iterations per CUDA graph, "
-                       "targets rendered at the true pose, start perturbed 3 cm / 2 deg",
+                       f"opaque surfaces with a 10 cm texture, one 640x480 frame, {iters} "
+                       "Gauss-Newton iterations per CUDA graph, targets rendered at the true "
+                       "pose, start perturbed 3 cm / 2 deg",
            "unit": "iters/s"}
+    ceil = l2_ceilings()
     for storage, method in (("f32", "lm"), ("bf16", "lm"), ("f32", "gn")):
         grid = plx.Grid.from_scene(sc.grid, storage)
         cams = plx.CameraSet([cam])
@@ -619,24 +751,27 @@ def run_tracking(args, world, rank, barrier):
         cams.poses.copy_(pose_now)
         rec = 896.0 if storage == "f32" else 448.0
         it_bytes = float((cnt[:, 0] * 32.0 + cnt[:, 1] * rec).sum() + 16.0 * cnt.shape[0])
-        hbm, peak_kind = peaks()
+        # the vertices the frame's rays composite with (untimed: nonzero rows
+        # of the grid adjoint at the start pose)
+        gfw = plx.render_forward(grid, cams, o)
+        gr, _ = plx.render_backward_grid(grid, cams, o, rgb_t, depth_t, gfw["rgb"], gfw["depth"])
+        touched = int((gr[:, :28] != 0).any(1).sum())
+        del gr, gfw
+        compulsory = touched * (rec / 7.0 + 4.0) + 16.0 * cnt.shape[0]
         res = {"value": iters * len(ms) / (sum(ms) / 1e3),
                "ms_per_iter": ms_it,
-               "roofline": {"bound": "hbm", "bytes_per_iter": it_bytes,
-                            "achieved": it_bytes / (ms_it / 1e3) / 1e9, "peak": hbm,
-                            "unit": "GB/s", "frac": it_bytes / (ms_it / 1e3) / 1e9 / hbm,
-                            "peak_kind": f"{peak_kind} copy bandwidth",
-                            "model": "the method's fixed no-reuse model: per ray 32 B of links "
-                                     "per marched sample, 896 B (f32) / 448 B (16-bit) per "
-                                     "sample with an allocated corner, 16 B of targets"},
+               "roofline": roofline_block(
+                   "backward_pose", args.tracking_workload, storage, cnt.shape[0], ms_it, ceil,
+                   compulsory, it_bytes,
+                   "compulsory bytes: each vertex the frame's rays composite with read once "
+                   "(its 128 B FP32 / 64 B 16-bit record) with its 4 B link, 16 B of targets "
+                   "per ray", clk),
                "step": ("Gauss-Newton with Marquardt damping, accept/reject on the loss "
                         "(plx_pose_step_lm)" if method == "lm" else
                         "undamped Gauss-Newton (plx_pose_step)"),
                "launch_config": grid.get_config(),
-               "start_err_cm_deg": [float(100 * np.abs(T0[:, 3] - cam.T_wc[:, 3]).max()),
-                                    float(np.degrees(np.abs(T0[:, :3] - cam.T_wc[:, :3]).max()))],
-               "final_err_cm_deg": [float(100 * np.abs(T[:, 3] - cam.T_wc[:, 3]).max()),
-                                    float(np.degrees(np.abs(T[:, :3] - cam.T_wc[:, :3]).max()))],
+               "start_err_cm_deg": list(pose_error(T0, cam.T_wc)),
+               "final_err_cm_deg": list(pose_error(T, cam.T_wc)),
                "final_loss": float(loss[0].item())}
         out[storage if method == "lm" else "gn_undamped_f32"] = res
         grid.close()
@@ -683,15 +818,68 @@ def run_tracking(args, world, rank, barrier):
         out["adam"][storage] = {
             "value": aiters * len(ms) / (sum(ms) / 1e3), "unit": "iters/s",
             "ms_per_frame": sum(ms) / len(ms),
-            "start_err_cm_deg": [float(100 * np.abs(T0[:, 3] - cam.T_wc[:, 3]).max()),
-                                 float(np.degrees(np.abs(T0[:, :3] - cam.T_wc[:, :3]).max()))],
-            "final_err_cm_deg": [float(100 * np.abs(T[:, 3] - cam.T_wc[:, 3]).max()),
-                                 float(np.degrees(np.abs(T[:, :3] - cam.T_wc[:, :3]).max()))],
+            "start_err_cm_deg": list(pose_error(T0, cam.T_wc)),
+            "final_err_cm_deg": list(pose_error(T, cam.T_wc)),
             "final_loss": float(buf[2][0].item())}
         grid.close()
     out["value"] = out["f32"]["value"]
     out["roofline"] = out["f32"]["roofline"]
     return out
+
+
+def run_small_bench(args, barrier):
+    """The small plain-FP32 workload: the dense 64^3 sphere grid, one 64x48
+    frame (3,072 rays), targets rendered on the GPU from the perturbed copy of
+    the grid. One step = forward + RGB-D loss + grid adjoint (re-marching, no
+    sample cache) + pose Jacobian with its FP64 reduction, back to back on one
+    stream. Its 29 MB grid sits in L2; the step is launch- and latency-bound
+    at this size (a few microseconds per kernel)."""
+    import torch
+
+    from paper_2307_03404_b300 import plx, scenes
+
+    g, cam, gp = scenes.sphere_scene()
+    opts = plx.opts_from_dict(dict(step=0.5 * float(g.h[0]), lambda_d=1.0, depth_is_z=False))
+    cams = plx.CameraSet([cam])
+    tgrid = plx.Grid.from_scene(gp, "f32")
+    tg = plx.render_forward(tgrid, cams, opts)
+    rgb_t, depth_t = tg["rgb"].clone(), tg["depth"].clone()
+    tgrid.close()
+    grid = plx.Grid.from_scene(g, "f32")
+    n_rays = cam.width * cam.height
+    fw = plx.render_forward(grid, cams, opts)
+    grad = torch.zeros(grid.n_alloc, plx.GRAD_STRIDE, device="cuda")
+    loss = torch.empty(2, device="cuda", dtype=torch.float64)
+    pose_out = (torch.empty(6, 6, device="cuda", dtype=torch.float64),
+                torch.empty(6, device="cuda", dtype=torch.float64),
+                torch.empty(2, device="cuda", dtype=torch.float64))
+
+    def step():
+        grad.zero_()
+        plx.render_forward(grid, cams, opts, out=fw)
+        plx.render_backward_grid(grid, cams, opts, rgb_t, depth_t, fw["rgb"], fw["depth"],
+                                 grad=grad, loss=loss)
+        plx.render_backward_pose(grid, cams, 0, opts, rgb_t, depth_t, out=pose_out)
+
+    K = max(20, 10 * args.steps)
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        step()
+    e1.record()
+    barrier()
+    ms = e0.elapsed_time(e1) / K
+    cnt = plx.render_forward(grid, cams, opts, counts=True)["counts"].cpu().numpy()
+    grid.close()
+    return {"workload": "sphere64: dense 64^3 grid (262,144 vertices, FP32), one 64x48 frame "
+                        "(3,072 rays); forward + loss + grid adjoint + pose Jacobian per step",
+            "value": n_rays / (ms / 1e3), "unit": "rays/s", "ms_per_step": ms, "steps": K,
+            "S_all_mean": float(cnt[:, 0].mean()), "S_occ_mean": float(cnt[:, 1].mean()),
+            "loss": loss.cpu().tolist(), "gpu_launches_per_step": 4,
+            "timing": "K steps back to back between two CUDA events; the grid stays in L2"}
 
 
 def run_batch_bench(args, barrier):
@@ -892,22 +1080,20 @@ def run_large_bench(args, barrier):
     valid = np.isfinite(d) & (d > 0)
     fwd_b, bwd_b, s_all, s_occ = bytes_model(counts, storage, valid)
     hbm, peak_kind = peaks()
-    achieved = bwd_b / (bwd_ms / 1e3) / 1e9
-    compulsory = touched * (64 + 2 * 112 + 4)
+    compulsory = touched * (64 + 2 * 112 + 4) + 32.0 * int(valid.sum())
+    roof = roofline_block(
+        "backward_grid", "house1024", storage, n_rays, bwd_ms, l2_ceilings(), compulsory, bwd_b,
+        "compulsory bytes: per touched vertex its 64 B record once, 2 x 112 B of FP32 gradient "
+        "read-modify-write and 4 B of link; 32 B per valid ray")
+    roof.update({"step_no_reuse_frac": (fwd_b + bwd_b) / (hbm * 1e9) * 1e3 / step_ms,
+                 "S_all_mean": s_all, "S_occ_mean": s_occ, "touched_vertices": touched})
     out = {"workload": f"house1024: 1024^3 grid, {n_alloc} allocated "
                        f"({n_alloc / 1024 ** 3:.2%}), {storage} storage, 16 x 1200x680 keyframes "
                        f"({n_rays} rays), step 0.5 voxel, <= 2048 samples per ray; the adjoint "
                        "recomputes each ray's state (no per-sample state kept)",
            "value": n_rays / (step_ms / 1e3), "unit": "rays/s", "ms_per_step": step_ms,
            "kernels_ms": {"forward": fwd_ms, "backward_grid": bwd_ms},
-           "roofline": {"bound": "hbm", "kernel": "backward_grid", "achieved": achieved,
-                        "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                        "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_launch": bwd_b,
-                        "step_frac": (fwd_b + bwd_b) / (hbm * 1e9) * 1e3 / step_ms,
-                        "S_all_mean": s_all, "S_occ_mean": s_occ,
-                        "touched_vertices": touched,
-                        "compulsory_bytes_per_launch": compulsory,
-                        "compulsory_gbs": compulsory / (bwd_ms / 1e3) / 1e9},
+           "roofline": roof,
            "loss": loss_main, "launch_config": config_main,
            "autotuned": tuned is not None, "steps": K,
            "scope": "one GPU (under torchrun every rank runs it; rank 0's numbers)"}
@@ -925,8 +1111,8 @@ def run_large_bench(args, barrier):
             "value": n_rays / ((fc + bc) / 1e3), "unit": "rays/s", "ms_per_step": fc + bc,
             "kernels_ms": {"forward": fc, "backward_grid": bc},
             "sample_cache": cache_note({"cache": cache_res, "kept": kept}, n_rays),
-            "roofline_frac": bwd_b / (bc / 1e3) / 1e9 / hbm,
-            "as_run_frac": bwd_i / (bc / 1e3) / 1e9 / hbm,
+            "no_reuse_frac": bwd_b / (bc / 1e3) / 1e9 / hbm,
+            "as_run_no_reuse_frac": bwd_i / (bc / 1e3) / 1e9 / hbm,
             "launch_config": grid.get_config()}
     grid.close()
     return out
@@ -1029,6 +1215,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--map-frames", type=int, default=FRAMES_PER_RANK,
                     help="keyframes per rank of the mapping workload (8; fewer only for "
                          "profiler captures)")

@@ -81,6 +81,8 @@ class MapConfig:
     seed: int = 7
     sort_rays: bool = True      # order each step's random rays for coherence
     sample_cache: bool = True   # forward keeps compositing samples for the adjoint
+    cache_check_every: int = 50  # steps between looks at the cache's overflow
+    cache_max_overflow: float = 0.01  # re-size when more rays than this re-march
 
 
 @dataclasses.dataclass
@@ -118,7 +120,16 @@ def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: 
     """Grow the grid from the keyframes' depth, then ``cfg.iters`` RMSProp
     steps, each on ``cfg.rays_per_step`` rays drawn uniformly (with
     replacement) from all keyframe pixels. rgb/depth hold every pixel of every
-    keyframe in camera order. Returns per-step losses (device FP64 [iters])."""
+    keyframe in camera order. Returns per-step losses (device FP64 [iters])
+    and a record of the sample cache: its cap, every re-sizing, and the rays
+    that overflowed it (re-marched) at each check.
+
+    The cache is sized on the first ray set with headroom. As the grid's
+    values change, rays may composite more samples than the cap; those are
+    re-marched, correctly but slower. Every ``cache_check_every`` steps the
+    overflow of the step just taken is read (one device-to-host copy); above
+    ``cache_max_overflow`` of the rays the cache is rebuilt with a cap of
+    1.25 x that step's largest count."""
     dg.grow(cams, depth, cfg.band, depth_is_z=bool(opts.depth_is_z))
     sizes = torch.tensor([w * h for w, h in cams.sizes], device="cuda")
     offs = torch.cumsum(sizes, 0) - sizes
@@ -129,6 +140,7 @@ def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: 
     losses = torch.zeros(cfg.iters, 2, dtype=torch.float64, device="cuda")
     fw = None
     cache, oc = None, opts
+    cache_log = {"cap": [], "overflow": []}
     widths = torch.tensor([w for w, _ in cams.sizes], device="cuda")
     for it in range(cfg.iters):
         rows = torch.randint(0, total, (cfg.rays_per_step,), generator=gen, device="cuda")
@@ -150,9 +162,22 @@ def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: 
             # compositing samples than the cap is re-marched by the adjoint
             cache = plx.SampleCache.sized_for(dg.grid, cams, opts, rays=rays, headroom=1.5)
             oc = cache.opts(opts)
+            cache_log["cap"].append([0, cache.cap])
         fw = plx.render_forward(dg.grid, cams, oc, rays=rays, out=fw)
         plx.render_backward_grid(dg.grid, cams, oc, rgb_t, depth_t, fw["rgb"], fw["depth"],
                                  rays=rays, grad=grad, loss=losses[it])
+        if cache is not None and (it + 1) % cfg.cache_check_every == 0:
+            cnt = cache.counts()
+            over = int((cnt > cache.cap).sum().item())
+            cache_log["overflow"].append([it, over])
+            if over > cfg.cache_max_overflow * cnt.shape[0]:
+                cap = int(1.25 * int(cnt.max().item()) + 7) // 8 * 8
+                del oc, cache
+                cache = plx.SampleCache(cfg.rays_per_step, cap)
+                oc = cache.opts(opts)
+                cache_log["cap"].append([it + 1, cap])
+                if log:
+                    log(f"[map] step {it}: {over} rays overflowed the sample cache; cap -> {cap}")
         f = it / max(1, cfg.iters - 1)
         lr_d = cfg.lr_density * (cfg.lr_density_final / cfg.lr_density) ** f
         lr_s = cfg.lr_sh * (cfg.lr_sh_final / cfg.lr_sh) ** f
@@ -160,7 +185,7 @@ def map_offline(dg: DynamicGrid, cams: plx.CameraSet, rgb: torch.Tensor, depth: 
                          lr_density=lr_d)
         if log and (it % 250 == 0 or it == cfg.iters - 1):
             log(f"[map] step {it} loss {float(losses[it, 0]):.5f}")
-    return losses[:, 0]
+    return losses[:, 0], cache_log
 
 
 def mapping_metrics(grid: plx.Grid, cam_list, rgb_frames, depth_frames, opts, n_rays=100_000,
@@ -313,7 +338,7 @@ def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", de
     dg = DynamicGrid((R, R, R), g.lo, g.hi, storage)
     torch.cuda.synchronize()
     t0 = time.time()
-    losses = map_offline(dg, kcams, krgb, kdepth, opts, map_cfg, log=log)
+    losses, cache_log = map_offline(dg, kcams, krgb, kdepth, opts, map_cfg, log=log)
     torch.cuda.synchronize()
     t_map = time.time() - t0
     mm = mapping_metrics(dg.grid, cams_np, rgb, depth, opts)
@@ -336,6 +361,7 @@ def run(scene, n_frames=300, span=0.3, map_every=10, res=None, storage="f32", de
            "allocated": dg.n, "map_seconds": t_map, "map_steps": map_cfg.iters,
            "map_rays_per_step": map_cfg.rays_per_step,
            "map_loss_first_last": [float(losses[0]), float(losses[-1])],
+           "sample_cache": cache_log,
            "mapping": mm,
            "path_m": float(np.sum(np.linalg.norm(np.diff(gt[:, :, 3], axis=0), axis=1)))}
     out.update(tracked(track_cfg))

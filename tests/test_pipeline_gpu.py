@@ -41,6 +41,12 @@ def test_benched_sequence_tracks_to_its_end():
     out = pipeline.run(sc, per_frame=True,
                        extra_track_cfgs=[pipeline.TrackConfig(method="lm", lm_iters=10)])
     assert out["keyframes"] == 31
+    # the mapping's sample cache is watched and re-sized: after the last
+    # re-sizing at most 1% of a step's rays overflow it and re-march
+    log = out["sample_cache"]
+    last = log["cap"][-1][0]
+    after = [n for it, n in log["overflow"] if it >= last]
+    assert log["overflow"] and max(after, default=0) <= 0.01 * out["map_rays_per_step"]
     for res in (out, out["other_trackers"][0]):
         err = np.array(res["err_m"])
         assert res["median_err_m"] < 0.006, res["median_err_m"]
