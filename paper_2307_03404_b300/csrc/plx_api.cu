@@ -14,7 +14,7 @@
 
 namespace plx {
 void launch_forward(int store, int minb, const Common& P, float* rgb, float* depth, float* state,
-                    int32_t* counts, cudaStream_t s);
+                    int32_t* counts, int num_sms, cudaStream_t s);
 void launch_backward_grid(int store, int minb, const Common& P, const float* rgb_t,
                           const float* depth_t, const float* rgb, const float* depth, float* grad,
                           double* loss_out, unsigned long long* M, int num_sms, cudaStream_t s);
@@ -566,7 +566,7 @@ plx_status plx_render_forward(const plx_grid* g, const plx_cameras* cams, const 
   if (P.ct.n_rays > 0 && (!rgb_out || !depth_out))
     return fail(PLX_EINVAL, "render_forward: null rgb_out or depth_out");
   launch_forward(g->desc.storage, g->cfg.forward_blocks, P, rgb_out, depth_out, state_out, counts_out,
-                 (cudaStream_t)stream);
+                 g->num_sms, (cudaStream_t)stream);
   return launch_check("render_forward");
 }
 

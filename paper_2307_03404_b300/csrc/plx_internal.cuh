@@ -97,7 +97,8 @@ constexpr int kDefaultBatchBlocks = 1;
 constexpr int kDefaultFineSkip = PLX_FINE_ADJOINT | PLX_FINE_POSE | PLX_FINE_BATCH;
 constexpr int kFineShift = 1;         // second-level empty-space blocks: 2^1 cells per axis
 constexpr int kMaxSortedRays = 8192;  // Adam tracking: random rays put in image order up to this
-constexpr int64_t kSegRays = 16384;   // pose Jacobian: a warp per ray up to this many rays
+constexpr int64_t kSegRays = 16384;   // a warp per ray up to this many rays (forward, grid
+                                      // adjoint without a sample cache, pose Jacobian)
 
 struct GridView {
   const int32_t* links;           // [rz][ry][rx]
@@ -602,6 +603,56 @@ __device__ __forceinline__ void alpha_of(float x, float& alpha, float& keep) {
 }
 
 __device__ __forceinline__ bool depth_valid(float d) { return isfinite(d) && d > 0.f; }
+
+// Warp-per-ray compositing: lane L holds the local (T, S[3], SD) of its
+// segment of the ray's samples (marched from transmittance 1 and zero sums).
+// Front-to-back compositing composes segments as
+//   (T_a, S_a) o (T_b, S_b) = (T_a T_b, S_a + T_a S_b),
+// so an exclusive scan over the lanes gives each segment's entry state
+// (T0, S0, SD0: the transmittance and colour / depth sums of all samples
+// before it) and the full composition gives the ray's (Tn, C, D). The sums
+// are carried as float-float pairs through the scan, so that its five levels
+// of additions do not add to the rounding of the terms themselves (colours
+// that cancel, as identity-activated ones can, would otherwise lose about
+// 1e-8 absolute). All 32 lanes call it.
+__device__ __forceinline__ void seg_scan(float T, const float S[3], float SD, int lane,
+                                         float& T0, float S0[3], float& SD0, float& Tn,
+                                         float C[3], float& D) {
+  float iT = T;
+  ff acc[4] = {ffv(S[0]), ffv(S[1]), ffv(S[2]), ffv(SD)};
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float pT = __shfl_up_sync(0xffffffffu, iT, off);
+    ff prev[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      prev[q] = ffv(__shfl_up_sync(0xffffffffu, acc[q].h, off),
+                    __shfl_up_sync(0xffffffffu, acc[q].l, off));
+    if (lane >= off) {  // (earlier prefix) o (this lane's inclusive part)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ff prod = two_prod(pT, acc[q].h);
+        prod.l = fmaf(pT, acc[q].l, prod.l);
+        acc[q] = ff_add(prev[q], prod);
+      }
+      iT *= pT;
+    }
+  }
+  float e[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[q] = __shfl_up_sync(0xffffffffu, acc[q].h + acc[q].l, 1);
+  T0 = __shfl_up_sync(0xffffffffu, iT, 1);
+  if (lane == 0) {
+    T0 = 1.f;
+    e[0] = e[1] = e[2] = e[3] = 0.f;
+  }
+  S0[0] = e[0]; S0[1] = e[1]; S0[2] = e[2]; SD0 = e[3];
+  Tn = __shfl_sync(0xffffffffu, iT, 31);
+  C[0] = __shfl_sync(0xffffffffu, acc[0].h + acc[0].l, 31);
+  C[1] = __shfl_sync(0xffffffffu, acc[1].h + acc[1].l, 31);
+  C[2] = __shfl_sync(0xffffffffu, acc[2].h + acc[2].l, 31);
+  D = __shfl_sync(0xffffffffu, acc[3].h + acc[3].l, 31);
+}
 
 // pose <- exp(xi^) pose for the twist xi = (rho, phi) (Sec. 5.3: the pose is
 // optimised directly): Rodrigues' rotation, translation V rho, composed on the

@@ -8,10 +8,15 @@ namespace plx {
 // With cap > 0 (the sample cache on) the samples that composite are kept for
 // the grid adjoint: (sigma, colour) and k of the first cap of them, and their
 // number, in row `out` of the cache; returns that number (0 when off).
-template <int STORE, bool COUNT>
+// SEG: march only samples [k0, k1) as if they were the whole ray
+// (transmittance from 1, sums from 0, no background, no early stop, no
+// cache): the segment's local (T, C, D), combined across the lanes of a warp
+// by seg_scan.
+template <int STORE, bool COUNT, bool SEG = false>
 __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, const float Y[9],
                                              float C[3], float& D, float& T, int& n_all,
-                                             int& n_occ, int64_t out, int cap) {
+                                             int& n_occ, int64_t out, int cap, int k0 = 0,
+                                             int k1 = 0) {
   const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
   int cx = -1, cy = -1, cz = -1;
   bool empty = true;
@@ -22,7 +27,9 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
   T = 1.f;
   n_all = r.n;
   int kept = 0;
-  for (int k = 0; k < r.n; ++k) {
+  if constexpr (SEG) cap = 0;
+  const int k_end = SEG ? k1 : r.n;
+  for (int k = SEG ? k0 : 0; k < k_end; ++k) {
     const float kf = (float)k;
     int ix, iy, iz;
     float fx, fy, fz;
@@ -74,14 +81,16 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
     for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(wgt, col[ch], C[ch]);
     D = fmaf(wgt, t, D);
     T *= keep;
-    if (T < P.o.stop_T) {
+    if (!SEG && T < P.o.stop_T) {
       n_all = k + 1;
       break;
     }
   }
   if (cap > 0) P.o.ccount[out] = kept;
+  if constexpr (!SEG) {
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], C[ch]);
+    for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], C[ch]);
+  }
   return kept;
 }
 
@@ -239,10 +248,17 @@ __device__ __forceinline__ bool leave_cell(float* __restrict__ grad, const int32
   return true;
 }
 
-template <int STORE>
+// The re-march carries shared corners on face steps only (leave_cell_face):
+// with leave_cell's full carry it took 13.8 ms on room256 at two blocks per
+// SM (spilling) and 17.8 ms at one, against 11.4 ms.
+// SEG: samples [k0, k1) only, entered with transmittance T0 and prefix sums
+// S0, SD0 of the samples before k0 (from seg_scan), no early stop.
+template <int STORE, bool SEG = false>
 __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, const float Y[9],
                                                const float Cf[3], float Df, const float gC[3],
-                                               float gD, float* __restrict__ grad) {
+                                               float gD, float* __restrict__ grad, int k0 = 0,
+                                               int k1 = 0, float T0 = 1.f,
+                                               const float* S0 = nullptr, float SD0 = 0.f) {
   const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
   int cx = -1, cy = -1, cz = -1;
   bool empty = true, dirty = false;
@@ -253,8 +269,14 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
 #pragma unroll
   for (int c = 0; c < 8; ++c) clear_corner(gs[c], gc[c]);
   float S[3] = {0.f, 0.f, 0.f}, SD = 0.f, T = 1.f;
+  if constexpr (SEG) {
+    T = T0;
+    S[0] = S0[0]; S[1] = S0[1]; S[2] = S0[2];
+    SD = SD0;
+  }
   const float dt = r.dt;
-  for (int k = 0; k < r.n; ++k) {
+  const int k_end = SEG ? k1 : r.n;
+  for (int k = SEG ? k0 : 0; k < k_end; ++k) {
     const float kf = (float)k;
     int ix, iy, iz;
     float fx, fy, fz;
@@ -313,7 +335,7 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
     }
     dirty = true;
     T = Tn;
-    if (T < P.o.stop_T) break;
+    if (!SEG && T < P.o.stop_T) break;
   }
   if (dirty) flush_cell(grad, l, gs, gc, Y);
 }

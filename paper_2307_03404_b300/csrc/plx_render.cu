@@ -55,6 +55,56 @@ k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __re
   }
 }
 
+// Warp-per-ray forward for few rays (a frame of a few thousand pixels leaves
+// most of the GPU idle one ray per thread, and each warp waits on its slowest
+// ray): the 32 lanes march consecutive segments of one ray and seg_scan
+// composites them. Needs stop_T = 0 and no sample cache (the caller checks).
+template <int STORE, bool COUNT, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
+k_forward_seg(const __grid_constant__ Common P, float* __restrict__ rgb,
+              float* __restrict__ depth, float* __restrict__ state, int32_t* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_slots = P.ct.n_tiles * 32;
+  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
+  for (int64_t ray = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); ray < n_slots;
+       ray += warps) {
+    const RayId id = ray_of(P, ray >> 5, (int)(ray & 31));
+    RayF r;
+    setup_ray(P, id, r, lane);
+    if (!id.valid) {  // warp-uniform: every lane has the same ray
+      if (lane == 0 && !P.ct.dense && id.out < P.ct.n_rays) {  // bad list entry: loud NaN
+        const float nan = __int_as_float(0x7fc00000);
+        rgb[3 * id.out] = rgb[3 * id.out + 1] = rgb[3 * id.out + 2] = nan;
+        depth[id.out] = nan;
+      }
+      continue;
+    }
+    float Y[9];
+    sh_basis(r.dir, Y);
+    const int k0 = (int)(((int64_t)r.n * lane) >> 5), k1 = (int)(((int64_t)r.n * (lane + 1)) >> 5);
+    float S[3], SD, T;
+    int n_all = 0, n_occ = 0;
+    march_forward<STORE, COUNT, true>(P, r, Y, S, SD, T, n_all, n_occ, id.out, 0, k0, k1);
+    float T0, S0[3], SD0, Tn, C[3], D;
+    seg_scan(T, S, SD, lane, T0, S0, SD0, Tn, C, D);
+    if (COUNT) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) n_occ += __shfl_xor_sync(0xffffffffu, n_occ, off);
+    }
+    if (lane == 0) {
+      rgb[3 * id.out] = fmaf(Tn, P.o.bg[0], C[0]);
+      rgb[3 * id.out + 1] = fmaf(Tn, P.o.bg[1], C[1]);
+      rgb[3 * id.out + 2] = fmaf(Tn, P.o.bg[2], C[2]);
+      depth[id.out] = D;
+      if (state) state[id.out] = Tn;
+      if (COUNT) {
+        counts[2 * id.out] = r.n;
+        counts[2 * id.out + 1] = n_occ;
+      }
+    }
+  }
+}
+
 __global__ void k_count_valid(const float* __restrict__ depth_t, int64_t n,
                               unsigned long long* __restrict__ M) {
   unsigned long long local = 0;
@@ -139,6 +189,50 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
   if (loss_out) add_warp_loss(loss, loss_out, Mc, lane);
 }
 
+// Warp-per-ray grid adjoint for few rays, without a sample cache: each lane
+// marches its segment of the ray once for the local (T, S, SD), seg_scan
+// gives the segment's entry transmittance and prefix sums, and the lane
+// re-marches the segment from them with the per-sample adjoint of Eq. 8-10
+// (the same arithmetic as march_backward), flushing its own corners. Needs
+// stop_T = 0.
+template <int STORE, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
+k_backward_grid_seg(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
+                    const float* __restrict__ depth_t, const float* __restrict__ rgb,
+                    const float* __restrict__ depth, float* __restrict__ grad,
+                    double* __restrict__ loss_out, const unsigned long long* __restrict__ Mc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_slots = P.ct.n_tiles * 32;
+  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
+  const bool loss_only = grad == nullptr;
+  const unsigned long long M = *Mc;
+  float loss = 0.f;
+  for (int64_t ray = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); ray < n_slots;
+       ray += warps) {
+    const RayId id = ray_of(P, ray >> 5, (int)(ray & 31));
+    RayF r;
+    setup_ray(P, id, r, lane);
+    if (!id.valid || M == 0) continue;  // warp-uniform
+    const float dz = __ldg(depth_t + id.out);
+    if (!depth_valid(dz)) continue;
+    float Cf[3], gC[3], Df, gD;
+    const float e = ray_residual(P, r, id.out, dz, (float)(1.0 / (double)M), rgb_t, rgb, depth,
+                                 Cf, gC, Df, gD);
+    if (lane == 0) loss += e;
+    if (loss_only) continue;
+    float Y[9];
+    sh_basis(r.dir, Y);
+    const int k0 = (int)(((int64_t)r.n * lane) >> 5), k1 = (int)(((int64_t)r.n * (lane + 1)) >> 5);
+    float S[3], SD, T;
+    int n_all = 0, n_occ = 0;
+    march_forward<STORE, false, true>(P, r, Y, S, SD, T, n_all, n_occ, id.out, 0, k0, k1);
+    float T0, S0[3], SD0, Tn, C[3], D;
+    seg_scan(T, S, SD, lane, T0, S0, SD0, Tn, C, D);
+    march_backward<STORE, true>(P, r, Y, Cf, Df, gC, gD, grad, k0, k1, T0, S0, SD0);
+  }
+  if (loss_out) add_warp_loss(loss, loss_out, Mc, lane);
+}
+
 // The grid adjoint from the sample cache: every valid ray's loss term, and the
 // gradients of the rays whose compositing samples all fit in it.
 template <int MINB>
@@ -174,9 +268,35 @@ k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict
 }
 
 // ------------------------------------------------------------ host launch
+// Few rays, no early stop, no sample cache and the sigmoid colour: a warp per
+// ray. (With identity colours, kept for closed-form tests, terms of both signs
+// can cancel to a colour near zero, where summing in the scan's order instead
+// of front to back costs about 1e-8 absolute, over 1e-5 of a 1e-3 floor.)
+static bool use_seg(const Common& P) {
+  return P.ct.n_tiles * 32 <= kSegRays && !(P.o.stop_T > 0.f) && P.o.ccap == 0 &&
+         P.o.color_act == PLX_ACT_SIGMOID;
+}
+
+static unsigned seg_blocks(const Common& P, int num_sms) {
+  const int64_t want = (P.ct.n_tiles * 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t cap = (int64_t)num_sms * 2;
+  return (unsigned)(want < cap ? want : cap);
+}
+
 void launch_forward(int store, int minb, const Common& P, float* rgb, float* depth, float* state,
-                    int32_t* counts, cudaStream_t s) {
+                    int32_t* counts, int num_sms, cudaStream_t s) {
   if (P.ct.n_tiles == 0) return;
+  if (use_seg(P)) {
+    const unsigned sb = seg_blocks(P, num_sms);
+#define PLX_FWD_SEG(S, M)                                                               \
+  if (counts)                                                                           \
+    k_forward_seg<S, true, M><<<sb, kBlock, 0, s>>>(P, rgb, depth, state, counts);      \
+  else                                                                                  \
+    k_forward_seg<S, false, M><<<sb, kBlock, 0, s>>>(P, rgb, depth, state, counts)
+    PLX_DISPATCH_SM(store, minb, PLX_FWD_SEG);
+#undef PLX_FWD_SEG
+    return;
+  }
   const unsigned blocks = (unsigned)((P.ct.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
 #define PLX_FWD(S, M)                                                               \
   if (counts)                                                                       \
@@ -208,6 +328,15 @@ void launch_backward_grid(int store, int minb, const Common& P, const float* rgb
       k_backward_grid_cached<2><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad,
                                                           loss_out, M);
     loss_full = nullptr;
+  }
+  if (use_seg(P)) {
+    const unsigned sb = seg_blocks(P, num_sms);
+#define PLX_BWD_SEG(S, M_)                                                                   \
+  k_backward_grid_seg<S, M_><<<sb, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad,     \
+                                                   loss_full, M)
+    PLX_DISPATCH_SM(store, minb, PLX_BWD_SEG);
+#undef PLX_BWD_SEG
+    return;
   }
 #define PLX_BWD(S, M_)                                                                   \
   k_backward_grid<S, M_><<<blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, rgb, depth, grad, \
