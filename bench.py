@@ -690,7 +690,13 @@ def run_tracking(args, world, rank, barrier, clk=None):
                        "pose, start perturbed 3 cm / 2 deg",
            "unit": "iters/s"}
     ceil = l2_ceilings()
-    for storage, method in (("f32", "lm"), ("bf16", "lm"), ("f32", "gn")):
+    o_exact = o
+    for storage, method, stop in (("f32", "lm", 0.0), ("bf16", "lm", 0.0), ("f32", "gn", 0.0),
+                                  ("f32", "lm", 1e-4)):
+        # stop > 0: rays stop once their transmittance falls below it (the
+        # targets are rendered the same way); in the opaque room that is just
+        # behind the first surface
+        o = plx.opts_from_dict(dict(opts, stop_T=stop)) if stop > 0 else o_exact
         grid = plx.Grid.from_scene(sc.grid, storage)
         cams = plx.CameraSet([cam])
         tg = plx.render_forward(grid, cams, o)       # targets at the true pose
@@ -773,7 +779,14 @@ def run_tracking(args, world, rank, barrier, clk=None):
                "start_err_cm_deg": list(pose_error(T0, cam.T_wc)),
                "final_err_cm_deg": list(pose_error(T, cam.T_wc)),
                "final_loss": float(loss[0].item())}
-        out[storage if method == "lm" else "gn_undamped_f32"] = res
+        if stop > 0:
+            res["stop_T"] = stop
+            res["note"] = ("rays stop once T < stop_T (targets rendered the same way): every "
+                           "rendered value within stop_T x max |colour| of the exact render; "
+                           "compare ms_per_iter with f32")
+            out["f32_stop_T"] = res
+        else:
+            out[storage if method == "lm" else "gn_undamped_f32"] = res
         grid.close()
     # the paper's tracker (Sec. 5.4): Adam on random rays of the frame
     n_rays, lr, aiters = args.adam_rays, args.adam_lr, args.adam_iters

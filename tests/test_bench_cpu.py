@@ -34,3 +34,41 @@ def test_committed_profile_records_name_their_capture():
     for r in recs:
         assert r["command"].startswith("ncu ") and "--clock-control none" in r["command"]
         assert r["rays_per_launch"] > 0 and r["dram_bytes_per_launch"] > 0
+
+
+def test_roofline_bound_is_the_closest_ceiling(monkeypatch):
+    """roofline_block: with an ncu record the bound is whichever fraction is
+    largest (L2 reductions, L2 reads, instruction issue); without one it is
+    the HBM roofline of the compulsory bytes; the no-reuse model is only a
+    diagnostic beside it."""
+    ceil = {"red_per_s": 200e9, "gather_float4_per_s": 300e9}
+    rec = {"kernel": "backward_grid", "workload": "w", "storage": "f32",
+           "dram_bytes_per_launch": 1e9, "warp_instructions_per_launch": 1.2e9,
+           "red_requests_per_launch": 0.5e9, "read_requests_per_launch": 1e6,
+           "rays_per_launch": 1000}
+    monkeypatch.setattr(bench, "measured_profile", lambda k, w, s: rec)
+    monkeypatch.setattr(bench, "peaks", lambda: (6500.0, "measured"))
+    clocks = {"sm_mhz": 2000.0}
+    import types
+    import sys
+
+    fake_torch = types.SimpleNamespace(cuda=types.SimpleNamespace(
+        current_device=lambda: 0,
+        get_device_properties=lambda d: types.SimpleNamespace(multi_processor_count=100)))
+    monkeypatch.setitem(sys.modules, "torch", fake_torch)
+    # 5 ms launch over 2000 rays: 1e9 reductions -> 200 G/s = 1.0 of the ceiling;
+    # 2.4e9 warp instructions / 5 ms = 480 G/s against 100 x 4 x 2e9 = 800 G/s
+    b = bench.roofline_block("backward_grid", "w", "f32", 2000, 5.0, ceil, 1e8, 1e12, "m",
+                             clocks)
+    assert b["bound"] == "l2_atomic" and abs(b["frac"] - 1.0) < 1e-12
+    assert abs(b["issue"]["frac"] - 0.6) < 1e-12
+    assert abs(b["hbm"]["frac"] - (1e8 / 5e-3 / 1e9) / 6500.0) < 1e-12
+    assert b["no_reuse"]["frac"] > 1 and b["traffic"] == 2e9
+    rec["red_requests_per_launch"] = 0.1e9          # now issue is the closest
+    b = bench.roofline_block("backward_grid", "w", "f32", 2000, 5.0, ceil, 1e8, 1e12, "m",
+                             clocks)
+    assert b["bound"] == "alu" and abs(b["frac"] - 0.6) < 1e-12
+    monkeypatch.setattr(bench, "measured_profile", lambda k, w, s: None)
+    b = bench.roofline_block("backward_grid", "w", "f32", 2000, 5.0, ceil, 1e8, 1e12, "m",
+                             clocks)
+    assert b["bound"] == "hbm" and b["unit"] == "GB/s" and b["traffic"] is None
