@@ -510,6 +510,30 @@ def test_upload_replaces_values(sphere):
     assert rel_err(got["rgb"], ref.rgb) <= TOL_FWD
 
 
+@pytest.mark.parametrize("width,height", [(128, 128), (128, 130)])
+def test_warp_per_ray_threshold(width, height):
+    """16,384 rays take the warp-per-ray forward and adjoint (a warp marches
+    segments of one ray and composes them by a scan), 16,640 the
+    one-ray-per-thread kernels: both against the oracle, FP32 bounds."""
+    g, cam0, gp = scenes.sphere_scene(width=width, height=height, f=120.0)
+    opts = dict(step=0.5 * g.h[0], lambda_d=0.7, bg=(0.1, 0.2, 0.3), depth_is_z=False)
+    tg = oracle.render(gp, [cam0], opts)
+    rgb_t, depth_t = tg.rgb.astype(np.float32), tg.depth.astype(np.float32)
+    case = GpuCase(g, [cam0])
+    got = case.forward(opts)
+    ref = oracle.render(g, [cam0], opts)
+    assert rel_err(got["rgb"], ref.rgb) <= TOL_FWD
+    assert rel_err(got["depth"], ref.depth) <= TOL_FWD
+    np.testing.assert_array_equal(got["counts"][:, 0], ref.n_marched)
+    np.testing.assert_array_equal(got["counts"][:, 1], ref.n_alloc)
+    gd, gs, _, loss = case.backward_grid(opts, rgb_t, depth_t)
+    rg = oracle.grad_grid(g, [cam0], opts, rgb_t, depth_t)
+    assert loss[1] == rg.M and abs(loss[0] - rg.loss) <= 1e-5 * rg.loss
+    assert norm_err(gd, rg.grad_density) <= TOL_GRAD
+    assert norm_err(gs, rg.grad_sh) <= TOL_GRAD
+    case.close()
+
+
 # ------------------------------------------------ full-size room, sampled
 @pytest.fixture(scope="module")
 def room256():
