@@ -788,6 +788,7 @@ def run_tracking(args, world, rank, barrier, clk=None):
         else:
             out[storage if method == "lm" else "gn_undamped_f32"] = res
         grid.close()
+    o = o_exact  # the exact options again (the loop above ended on the early-stop variant)
     # the paper's tracker (Sec. 5.4): Adam on random rays of the frame
     n_rays, lr, aiters = args.adam_rays, args.adam_lr, args.adam_iters
     for storage in ("f32", "bf16"):

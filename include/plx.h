@@ -271,7 +271,7 @@ plx_status plx_render_backward_pose(const plx_grid *grid,
  *   desc    HOST descriptor (res, lo, hi, n_alloc, storage)
  *   links   DEVICE int32 [res_z][res_y][res_x]; each entry -1 or in
  *           [0, n_alloc). NOT checked here (plx_grid_create checks them).
- *   records DEVICE, 16-byte aligned, one record per allocated vertex in the
+ *   records DEVICE, 32-byte aligned, one record per allocated vertex in the
  *           layout of desc->storage: PLX_STORE_F32 = 32 floats (slot 0
  *           density, slots 1..27 SH in canonical order, 28..31 ignored);
  *           PLX_STORE_BF16 / PLX_STORE_F16 = 32 16-bit values in the same

@@ -892,8 +892,8 @@ extern "C" plx_status plx_render_backward_pose_noalloc(
     return fail(PLX_EINVAL, "%s: unknown storage %d", what, desc->storage);
   if (!links || (desc->n_alloc > 0 && !records))
     return fail(PLX_EINVAL, "%s: null links or records", what);
-  if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
-    return fail(PLX_EINVAL, "%s: records must be 16-byte aligned", what);
+  if (reinterpret_cast<uintptr_t>(records) % 32 != 0)  // read with 256-bit loads
+    return fail(PLX_EINVAL, "%s: records must be 32-byte aligned", what);
   if (cam < 0) return fail(PLX_EINVAL, "%s: cam < 0", what);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
