@@ -68,6 +68,7 @@ def combine_rank_times(times_ms, units_per_rank):
 KERNEL_SOURCES = {
     "forward": ("plx_internal.cuh", "plx_march.cuh", "plx_render.cu"),
     "backward_grid": ("plx_internal.cuh", "plx_march.cuh", "plx_render.cu"),
+    "backward_grid_cached": ("plx_internal.cuh", "plx_march.cuh", "plx_render.cu"),
     "backward_pose": ("plx_internal.cuh", "plx_pose_march.cuh", "plx_pose.cu"),
 }
 
@@ -145,9 +146,11 @@ def l2_ceilings(rows=600_000, reps=5):
     """Rates the memory system sustains for the mapping kernels' L2 accesses,
     measured live with the library's probe kernels (plx_probe) over a buffer of
     ``rows`` 128-byte rows (the size of the set of vertices one room256 step
-    touches, so it stays in L2): float4 reductions into random rows (7 per row,
-    as the adjoint's corner flush) and float4 gathers of random rows (as the
-    record gathers). Best of 8 and 16 blocks of 256 threads per SM."""
+    touches, so it stays in L2): float4 reductions into random rows, 7 per
+    row, sent per lane (as the re-marching adjoint's corner flush) and as one
+    coalesced request per row (as the sample-cache adjoint's warp-cooperative
+    flush), and float4 gathers of random rows (as the record gathers). Best of
+    8 and 16 blocks of 256 threads per SM."""
     import torch
 
     from paper_2307_03404_b300 import plx
@@ -155,7 +158,9 @@ def l2_ceilings(rows=600_000, reps=5):
     buf = torch.zeros(rows, plx.GRAD_STRIDE, device="cuda")
     sms = torch.cuda.get_device_properties(buf.device).multi_processor_count
     out = {}
-    for kind, name in ((plx.PROBE_RED, "red"), (plx.PROBE_GATHER, "gather")):
+    # units per lane and operation: 7 float4 (RED, GATHER) or 1 row (RED_ROWS)
+    for kind, name, per in ((plx.PROBE_RED, "red", 7), (plx.PROBE_GATHER, "gather", 7),
+                            (plx.PROBE_RED_ROWS, "red_rows", 1)):
         best = 0.0
         for bps in (8, 16):
             blocks, ops = bps * sms, 32
@@ -169,14 +174,21 @@ def l2_ceilings(rows=600_000, reps=5):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            best = max(best, blocks * 256 * ops * 7 / (ms / 1e3))
+            best = max(best, blocks * 256 * ops * per / (ms / 1e3))
         out[name] = best
     del buf
-    return {"red_per_s": out["red"], "gather_float4_per_s": out["gather"],
-            "buffer_MB": rows * 128 / 1e6,
+    return {"red_per_s": out["red"], "red_rows_per_s": out["red_rows"],
+            "gather_float4_per_s": out["gather"], "buffer_MB": rows * 128 / 1e6,
             "how": "plx_probe: each lane 32 times picks a random 128-byte row of the buffer and "
-                   "issues 7 float4 atomic adds (red) or 7 float4 loads (gather) to it; best of "
-                   "8 and 16 blocks of 256 threads per SM, CUDA events over 5 launches"}
+                   "issues 7 float4 atomic adds (red, per float4) or 7 float4 loads (gather); "
+                   "red_rows: the same rows and adds, 7 lanes per row with one float4 each "
+                   "(one coalesced request per row, per row); best of 8 and 16 blocks of 256 "
+                   "threads per SM, CUDA events over 5 launches"}
+
+
+# how each adjoint kernel sends a corner's 7 float4 reductions: per lane (7 L2
+# requests) or warp-cooperatively (one coalesced request per row)
+SCATTER_FORM = {"backward_grid": "lanes", "backward_grid_cached": "rows"}
 
 
 def l2_roofline(kernel, workload, storage, n_rays, ms, ceil):
@@ -184,9 +196,14 @@ def l2_roofline(kernel, workload, storage, n_rays, ms, ceil):
     (lts__t_requests_srcunit_tex_op_red.sum) and read requests
     (lts__t_requests_srcunit_tex_op_read.sum) per launch from the ncu record
     of profiles/traffic.json (taken on the current sources, scaled to n_rays
-    rays) over the launch time measured here. None where no record matches."""
+    rays) over the launch time measured here. A kernel that sends each
+    corner's row as one coalesced request (SCATTER_FORM "rows") is held
+    against the probe's coalesced-row rate, one that sends 7 per-lane float4
+    requests against the per-float4 rate. None where no record matches."""
     out = {}
-    for key, name, peak in (("red_requests_per_launch", "red", ceil["red_per_s"]),
+    red_peak = (ceil["red_rows_per_s"] if SCATTER_FORM.get(kernel) == "rows"
+                else ceil["red_per_s"])
+    for key, name, peak in (("red_requests_per_launch", "red", red_peak),
                             ("read_requests_per_launch", "read", ceil["gather_float4_per_s"])):
         n = measured_traffic(kernel, workload, storage, n_rays, key=key)
         if n:
@@ -237,7 +254,8 @@ def roofline_block(kernel, workload, storage, n_rays, ms, ceil, compulsory, no_r
                                "record (profiles/traffic.json, taken on the current sources, "
                                "scaled by rays) over the launch time measured here: L2 "
                                "reduction / read requests against the rate plx_probe measures "
-                               "live for the same access (float4 reductions or gathers of "
+                               "live for the same access (float4 reductions, per lane or "
+                               "coalesced per row as the kernel sends them, or gathers of "
                                "random 128-byte rows in L2), and warp instructions against "
                                "one per clock per SM sub-partition at the sampled clock "
                                "(alu); bound = the largest of these fractions"})
@@ -562,9 +580,12 @@ def run_ours(args):
     fwd_b, bwd_b, s_all, s_occ = bytes_model(main["counts"], args.storage, valid)
     fwd_i, bwd_i, _, _ = bytes_model(main["counts"], args.storage, valid, main["kept"], cap_main)
     fwd_ms, bwd_ms = statistics.mean(main["fwd_ms"]), statistics.mean(main["bwd_ms"])
-    dom = "backward_grid" if bwd_ms >= fwd_ms else "forward"
-    dom_b, dom_ms = (bwd_b, bwd_ms) if dom == "backward_grid" else (fwd_b, fwd_ms)
-    dom_i = bwd_i if dom == "backward_grid" else fwd_i
+    # the adjoint launch that does the work: the sample-cache kernel (its
+    # re-marching partner only takes overflowing rays) or the re-march
+    bwd_name = "backward_grid_cached" if main["cache"] else "backward_grid"
+    dom = bwd_name if bwd_ms >= fwd_ms else "forward"
+    dom_b, dom_ms = (bwd_b, bwd_ms) if dom == bwd_name else (fwd_b, fwd_ms)
+    dom_i = bwd_i if dom == bwd_name else fwd_i
     achieved = dom_b / (dom_ms / 1e3) / 1e9
     step_roof = (fwd_b + bwd_b) / (hbm * 1e9) * 1e3   # ms per step at the HBM roof
     fo_b, bo_b, _, _ = bytes_model(other["counts"], other_storage, valid)

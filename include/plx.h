@@ -488,14 +488,20 @@ plx_status plx_render_batch(const plx_grid *grid, const plx_cameras *cams,
  *                     7 * ops * threads reductions per launch
  *   PLX_PROBE_GATHER  the same rows, 7 float4 loads each (read only)
  *   PLX_PROBE_STREAM  `ops` coalesced float4 passes over all rows (read only)
+ *   PLX_PROBE_RED_ROWS the same rows and additions as PLX_PROBE_RED, sent
+ *                     the way the sample-cache adjoint sends them: a warp
+ *                     instruction covers 4 rows, 7 lanes per row with one
+ *                     float4 each (one coalesced request per row);
+ *                     ops * threads rows per launch ('group' is ignored)
  *   buf     DEVICE float [n_rows][PLX_GRAD_STRIDE], 16-byte aligned, holding
  *           finite values (RED adds to them); 1 <= n_rows < 2^32
  *   blocks  thread blocks of 256 threads (1 .. 2^20); ops 1 .. 1024;
- *           group 1 .. 32 (ignored by STREAM)
+ *           group 1 .. 32 (ignored by STREAM and RED_ROWS)
  * Asynchronous. Errors: PLX_EINVAL, PLX_ECUDA. */
 #define PLX_PROBE_RED 0
 #define PLX_PROBE_GATHER 1
 #define PLX_PROBE_STREAM 2
+#define PLX_PROBE_RED_ROWS 3
 plx_status plx_probe(int32_t kind, float *buf, int64_t n_rows, int32_t group,
                      int32_t ops, int32_t blocks, void *stream);
 

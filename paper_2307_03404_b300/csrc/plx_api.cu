@@ -934,7 +934,8 @@ extern "C" plx_status plx_render_backward_pose_noalloc(
 extern "C" plx_status plx_probe(int32_t kind, float* buf, int64_t n_rows, int32_t group,
                                 int32_t ops, int32_t blocks, void* stream) {
   const char* what = "plx_probe";
-  if (kind != PLX_PROBE_RED && kind != PLX_PROBE_GATHER && kind != PLX_PROBE_STREAM)
+  if (kind != PLX_PROBE_RED && kind != PLX_PROBE_GATHER && kind != PLX_PROBE_STREAM &&
+      kind != PLX_PROBE_RED_ROWS)
     return fail(PLX_EINVAL, "%s: unknown kind %d", what, kind);
   if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15) != 0)
     return fail(PLX_EINVAL, "%s: buffer null or not 16-byte aligned", what);
@@ -942,7 +943,7 @@ extern "C" plx_status plx_probe(int32_t kind, float* buf, int64_t n_rows, int32_
     return fail(PLX_EINVAL, "%s: n_rows %lld out of [1, 2^32)", what, (long long)n_rows);
   if (ops < 1 || ops > 1024 || blocks < 1 || blocks > (1 << 20))
     return fail(PLX_EINVAL, "%s: ops %d or blocks %d out of range", what, ops, blocks);
-  if (kind != PLX_PROBE_STREAM && (group < 1 || group > 32))
+  if ((kind == PLX_PROBE_RED || kind == PLX_PROBE_GATHER) && (group < 1 || group > 32))
     return fail(PLX_EINVAL, "%s: group %d out of [1, 32]", what, group);
   launch_probe(kind, buf, (uint32_t)n_rows, group, ops, blocks, (cudaStream_t)stream);
   return launch_check(what);

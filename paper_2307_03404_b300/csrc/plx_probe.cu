@@ -10,7 +10,11 @@
 //                     operation, rows drawn at random from n_rows rows
 //                     (lanes in groups of `group` share a row: contention);
 //   PLX_PROBE_GATHER  7 float4 loads from one random row per lane and operation;
-//   PLX_PROBE_STREAM  coalesced float4 loads over all n_rows rows.
+//   PLX_PROBE_STREAM  coalesced float4 loads over all n_rows rows;
+//   PLX_PROBE_RED_ROWS the rows and additions of PLX_PROBE_RED, each row's 7
+//                     float4 sent by 7 lanes at once (lanes 8g..8g+6 of a
+//                     warp instruction cover row g of 4), as the sample-cache
+//                     adjoint's warp-cooperative scatter sends them.
 // Every access stays inside [buf, buf + n_rows * 128 bytes): rows are drawn as
 // (hash * n_rows) >> 32 < n_rows and the stream walks indices below n_rows * 8.
 #include "plx_internal.cuh"
@@ -42,6 +46,23 @@ k_probe_red(float* __restrict__ buf, uint32_t n_rows, int group, int ops) {
     float4* dst = reinterpret_cast<float4*>(buf + (uint64_t)row * PLX_GRAD_STRIDE);
 #pragma unroll
     for (int j = 0; j < 7; ++j) atomicAdd(dst + j, v);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_probe_red_rows(float* __restrict__ buf, uint32_t n_rows, int ops) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t g = lane >> 3, q = lane & 7;
+  const float4 v = make_float4(1e-7f, 1e-7f, 1e-7f, 1e-7f);
+  for (int it = 0; it < ops; ++it) {
+    // the warp's 32 rows of this operation (those of PLX_PROBE_RED with
+    // group 1), 4 per instruction
+#pragma unroll
+    for (uint32_t b = 0; b < 32; b += 4) {
+      const uint32_t row = probe_row((warp * 1024u + (uint32_t)it) * 32u + b + g, n_rows);
+      if (q < 7) atomicAdd(reinterpret_cast<float4*>(buf + (uint64_t)row * PLX_GRAD_STRIDE) + q, v);
+    }
   }
 }
 
@@ -83,6 +104,7 @@ void launch_probe(int kind, float* buf, uint32_t n_rows, int group, int ops, int
   switch (kind) {
     case PLX_PROBE_RED: k_probe_red<<<blocks, 256, 0, s>>>(buf, n_rows, group, ops); break;
     case PLX_PROBE_GATHER: k_probe_gather<<<blocks, 256, 0, s>>>(buf, n_rows, group, ops); break;
+    case PLX_PROBE_RED_ROWS: k_probe_red_rows<<<blocks, 256, 0, s>>>(buf, n_rows, ops); break;
     default: k_probe_stream<<<blocks, 256, 0, s>>>(buf, n_rows, ops); break;
   }
 }

@@ -243,26 +243,27 @@ k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict
                        double* __restrict__ loss_out, const unsigned long long* __restrict__ Mc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  __shared__ __align__(16) float stage[kWarpsPerBlock * stage_floats(32)];
   float loss = 0.f;
-  if (tile < P.ct.n_tiles) {
+  if (tile < P.ct.n_tiles) {  // the whole warp: the scatter is cooperative
     const RayId id = ray_of(P, tile, lane);
     RayF r;
     setup_ray(P, id, r, lane);
     const unsigned long long M = *Mc;
+    float Cf[3] = {0.f, 0.f, 0.f}, gC[3] = {0.f, 0.f, 0.f}, Df = 0.f, gD = 0.f, Y[9];
+    int n_kept = 0;
     if (id.valid && M > 0) {
       const float dz = __ldg(depth_t + id.out);
       if (depth_valid(dz)) {
-        float Cf[3], gC[3], Df, gD;
         loss = ray_residual(P, r, id.out, dz, (float)(1.0 / (double)M), rgb_t, rgb, depth, Cf,
                             gC, Df, gD);
-        const int n_kept = __ldg(P.o.ccount + id.out);
-        if (n_kept <= P.o.ccap) {
-          float Y[9];
-          sh_basis(r.dir, Y);
-          march_backward_cached(P, r, Y, Cf, Df, gC, gD, grad, id.out, n_kept);
-        }
+        const int nk = __ldg(P.o.ccount + id.out);
+        if (nk <= P.o.ccap) n_kept = nk;  // else the re-marching kernel takes the ray
       }
     }
+    sh_basis(r.dir, Y);
+    march_backward_cached_warp<32>(P, r, Y, Cf, Df, gC, gD, grad, id.out, n_kept,
+                                   stage + warp * stage_floats(32), lane);
   }
   if (loss_out) add_warp_loss(loss, loss_out, Mc, lane);
 }

@@ -232,6 +232,11 @@ def test_probe_argument_errors(lib):
     assert b"group" in lib.plx_last_error()
     assert lib.plx_probe(2, fake, 16, 1, 0, 1, None) == 1
     assert b"ops" in lib.plx_last_error()
+    # the coalesced-row reductions ignore `group`
+    assert lib.plx_probe(plx.PROBE_RED_ROWS, fake, 16, 99, 0, 1, None) == 1
+    assert b"ops" in lib.plx_last_error()
+    assert lib.plx_probe(4, fake, 16, 1, 1, 1, None) == 1
+    assert b"kind" in lib.plx_last_error()
 
 
 def test_sample_cache_options_keep_the_cache_alive():

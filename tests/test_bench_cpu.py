@@ -41,7 +41,7 @@ def test_roofline_bound_is_the_closest_ceiling(monkeypatch):
     largest (L2 reductions, L2 reads, instruction issue); without one it is
     the HBM roofline of the compulsory bytes; the no-reuse model is only a
     diagnostic beside it."""
-    ceil = {"red_per_s": 200e9, "gather_float4_per_s": 300e9}
+    ceil = {"red_per_s": 200e9, "red_rows_per_s": 40e9, "gather_float4_per_s": 300e9}
     rec = {"kernel": "backward_grid", "workload": "w", "storage": "f32",
            "dram_bytes_per_launch": 1e9, "warp_instructions_per_launch": 1.2e9,
            "red_requests_per_launch": 0.5e9, "read_requests_per_launch": 1e6,
@@ -68,6 +68,13 @@ def test_roofline_bound_is_the_closest_ceiling(monkeypatch):
     b = bench.roofline_block("backward_grid", "w", "f32", 2000, 5.0, ceil, 1e8, 1e12, "m",
                              clocks)
     assert b["bound"] == "alu" and abs(b["frac"] - 0.6) < 1e-12
+    # the sample-cache adjoint sends one coalesced request per row: its
+    # requests are held against the probe's row rate (0.1e9 x 2 / 5 ms = 40 G/s
+    # against 40 G/s, where the per-float4 rate gave 0.2 and "alu" won)
+    b = bench.roofline_block("backward_grid_cached", "w", "f32", 2000, 5.0, ceil, 1e8, 1e12,
+                             "m", clocks)
+    assert b["bound"] == "l2_atomic" and abs(b["frac"] - 1.0) < 1e-12
+    assert b["l2"]["red"]["peak"] == 40e9
     monkeypatch.setattr(bench, "measured_profile", lambda k, w, s: None)
     b = bench.roofline_block("backward_grid", "w", "f32", 2000, 5.0, ceil, 1e8, 1e12, "m",
                              clocks)
