@@ -103,7 +103,8 @@ k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
         march_backward_cached(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM, grad,
                                      cslot, kept);
       else
-        march_backward<STORE>(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM, grad);
+        march_backward<STORE, false, false>(P, r, Y, C, D, gC, 2.f * P.o.lambda_d * eD * invM,
+                                            grad);
     }
   }
   if (slot >= 0) atomicAdd(track_acc + 32 * slot + lane, acc);

@@ -150,9 +150,8 @@ __device__ __forceinline__ void carry_cell(float* __restrict__ grad, const int32
 // Leaves the current cell for the one (dx, dy, dz) away: if `carry` and the
 // step is to a face-adjacent cell, the shared face's sums move to their new
 // slots and the rest are flushed; otherwise all are flushed. Returns whether
-// carried sums remain in registers. The re-marching adjoint uses this form:
-// its longer loop pays for leave_cell's 26-way dispatch in spills and time
-// (13.8 against 11.4 ms on room256).
+// carried sums remain in registers. The re-march of the batched kernel uses
+// this form (its registers are the scarcest).
 __device__ __forceinline__ bool leave_cell_face(float* __restrict__ grad, const int32_t l[8],
                                            float gs[8], float gc[8][3], const float Y[9], int dx,
                                            int dy, int dz, bool carry) {
@@ -199,14 +198,32 @@ __device__ __forceinline__ void move_shared(float gs[8], float gc[8][3]) {
   }
 }
 
+// The register moves of move_shared<dx, dy, dz> for a step known only at run
+// time, as up to three one-axis moves: moving by dx along x, then dy along y,
+// then dz along z leaves slot n holding old corner n + (dx, dy, dz) when that
+// lies in the old cell on every axis and zero otherwise, which is the
+// diagonal move. Six short bodies instead of 26 keep the adjoint's loop small
+// enough for the instruction cache.
+__device__ __forceinline__ void move_by(int dx, int dy, int dz, float gs[8], float gc[8][3]) {
+  if (dx > 0) move_shared<1, 0, 0>(gs, gc);
+  else if (dx < 0) move_shared<-1, 0, 0>(gs, gc);
+  if (dy > 0) move_shared<0, 1, 0>(gs, gc);
+  else if (dy < 0) move_shared<0, -1, 0>(gs, gc);
+  if (dz > 0) move_shared<0, 0, 1>(gs, gc);
+  else if (dz < 0) move_shared<0, 0, -1>(gs, gc);
+}
+
 // Leaves the current cell for the one (dx, dy, dz) away. If `carry` and the
 // new cell touches the old one (every |d| <= 1), the corners the two cells
 // share are the same vertices: their sums stay in registers and move to their
 // new slots, and only the other corners are flushed (4 of 8 on a face step,
 // 6 on an edge step, 7 on a corner step); otherwise all are flushed. Returns
-// whether carried sums remain in registers. The sample-cache adjoint uses
-// this form: against carrying on face steps only it cuts its flushes from
-// 2.26 to 2.06 per kept sample and its time from 7.3 to 6.7 ms on room256.
+// whether carried sums remain in registers. Against carrying on face steps
+// only it cut the sample-cache adjoint's flushes from 2.26 to 2.06 per kept
+// sample on room256. AXIS: the moves by move_by (the re-marching adjoint),
+// else by one of 26 compile-time bodies (the batched kernel, where move_by
+// measured slower).
+template <bool AXIS>
 __device__ __forceinline__ bool leave_cell(float* __restrict__ grad, const int32_t l[8],
                                            float gs[8], float gc[8][3], const float Y[9], int dx,
                                            int dy, int dz, bool carry) {
@@ -228,32 +245,38 @@ __device__ __forceinline__ bool leave_cell(float* __restrict__ grad, const int32
     for (int c = 0; c < 8; ++c) clear_corner(gs[c], gc[c]);
     return false;
   }
-  switch ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)) {
-#define PLX_MOVE(X, Y_, Z)                                 \
-  case ((X) + 1) + 3 * ((Y_) + 1) + 9 * ((Z) + 1):         \
-    move_shared<X, Y_, Z>(gs, gc);                         \
+  if constexpr (AXIS) {
+    move_by(dx, dy, dz, gs, gc);
+  } else {
+    switch ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)) {
+#define PLX_MOVE(X, Y_, Z)                         \
+  case ((X) + 1) + 3 * ((Y_) + 1) + 9 * ((Z) + 1): \
+    move_shared<X, Y_, Z>(gs, gc);                 \
     break;
-    PLX_MOVE(-1, -1, -1) PLX_MOVE(0, -1, -1) PLX_MOVE(1, -1, -1)
-    PLX_MOVE(-1, 0, -1) PLX_MOVE(0, 0, -1) PLX_MOVE(1, 0, -1)
-    PLX_MOVE(-1, 1, -1) PLX_MOVE(0, 1, -1) PLX_MOVE(1, 1, -1)
-    PLX_MOVE(-1, -1, 0) PLX_MOVE(0, -1, 0) PLX_MOVE(1, -1, 0)
-    PLX_MOVE(-1, 0, 0) PLX_MOVE(1, 0, 0)
-    PLX_MOVE(-1, 1, 0) PLX_MOVE(0, 1, 0) PLX_MOVE(1, 1, 0)
-    PLX_MOVE(-1, -1, 1) PLX_MOVE(0, -1, 1) PLX_MOVE(1, -1, 1)
-    PLX_MOVE(-1, 0, 1) PLX_MOVE(0, 0, 1) PLX_MOVE(1, 0, 1)
-    PLX_MOVE(-1, 1, 1) PLX_MOVE(0, 1, 1) PLX_MOVE(1, 1, 1)
+      PLX_MOVE(-1, -1, -1) PLX_MOVE(0, -1, -1) PLX_MOVE(1, -1, -1)
+      PLX_MOVE(-1, 0, -1) PLX_MOVE(0, 0, -1) PLX_MOVE(1, 0, -1)
+      PLX_MOVE(-1, 1, -1) PLX_MOVE(0, 1, -1) PLX_MOVE(1, 1, -1)
+      PLX_MOVE(-1, -1, 0) PLX_MOVE(0, -1, 0) PLX_MOVE(1, -1, 0)
+      PLX_MOVE(-1, 0, 0) PLX_MOVE(1, 0, 0)
+      PLX_MOVE(-1, 1, 0) PLX_MOVE(0, 1, 0) PLX_MOVE(1, 1, 0)
+      PLX_MOVE(-1, -1, 1) PLX_MOVE(0, -1, 1) PLX_MOVE(1, -1, 1)
+      PLX_MOVE(-1, 0, 1) PLX_MOVE(0, 0, 1) PLX_MOVE(1, 0, 1)
+      PLX_MOVE(-1, 1, 1) PLX_MOVE(0, 1, 1) PLX_MOVE(1, 1, 1)
 #undef PLX_MOVE
-    default: break;  // (0, 0, 0): the same cell, not a step
+      default: break;  // (0, 0, 0): the same cell, not a step
+    }
   }
   return true;
 }
 
-// The re-march carries shared corners on face steps only (leave_cell_face):
-// with leave_cell's full carry it took 13.8 ms on room256 at two blocks per
-// SM (spilling) and 17.8 ms at one, against 11.4 ms.
+// FULL: carry the corners shared on face, edge and corner steps
+// (leave_cell<true>, the moves done axis by axis), else on face steps only.
+// The full carry with one of 26 move bodies per step took 13.8 against 11.4
+// ms on room256 (spills, code size); with the axis moves 10.7 against 10.9 ms
+// in FP32 and 8.7 against 12.2 ms in BF16.
 // SEG: samples [k0, k1) only, entered with transmittance T0 and prefix sums
 // S0, SD0 of the samples before k0 (from seg_scan), no early stop.
-template <int STORE, bool SEG = false>
+template <int STORE, bool SEG = false, bool FULL = true>
 __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, const float Y[9],
                                                const float Cf[3], float Df, const float gC[3],
                                                float gD, float* __restrict__ grad, int k0 = 0,
@@ -287,7 +310,8 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
       const int esh = empty_block_shift(P.g, ix, iy, iz);
       const bool skip = esh >= 0;
       if (dirty)  // carried sums still have to reach memory
-        dirty = leave_cell_face(grad, l, gs, gc, Y, ix - cx, iy - cy, iz - cz, !skip);
+        dirty = FULL ? leave_cell<true>(grad, l, gs, gc, Y, ix - cx, iy - cy, iz - cz, !skip)
+                     : leave_cell_face(grad, l, gs, gc, Y, ix - cx, iy - cy, iz - cz, !skip);
       cx = ix; cy = iy; cz = iz;
       if (skip) {
         empty = true;
@@ -374,7 +398,7 @@ __device__ __forceinline__ void march_backward_cached(const Common& P, const Ray
     sample_axis(r.B[1], r.S[1], k, rm2y, iy, fy);
     sample_axis(r.B[2], r.S[2], k, rm2z, iz, fz);
     if (ix != cx || iy != cy || iz != cz) {
-      if (dirty) dirty = leave_cell(grad, l, gs, gc, Y, ix - cx, iy - cy, iz - cz, true);
+      if (dirty) dirty = leave_cell<false>(grad, l, gs, gc, Y, ix - cx, iy - cy, iz - cz, true);
       cx = ix; cy = iy; cz = iz;
       load_links(P.g, ix, iy, iz, l);
     }
@@ -537,23 +561,7 @@ __device__ __forceinline__ void march_backward_cached_warp(
 #pragma unroll
           for (int c = 0; c < 8; ++c) clear_corner(gs[c], gc[c]);
         } else {
-          switch ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)) {
-#define PLX_MOVE(X, Y_, Z)                         \
-  case ((X) + 1) + 3 * ((Y_) + 1) + 9 * ((Z) + 1): \
-    move_shared<X, Y_, Z>(gs, gc);                 \
-    break;
-            PLX_MOVE(-1, -1, -1) PLX_MOVE(0, -1, -1) PLX_MOVE(1, -1, -1)
-            PLX_MOVE(-1, 0, -1) PLX_MOVE(0, 0, -1) PLX_MOVE(1, 0, -1)
-            PLX_MOVE(-1, 1, -1) PLX_MOVE(0, 1, -1) PLX_MOVE(1, 1, -1)
-            PLX_MOVE(-1, -1, 0) PLX_MOVE(0, -1, 0) PLX_MOVE(1, -1, 0)
-            PLX_MOVE(-1, 0, 0) PLX_MOVE(1, 0, 0)
-            PLX_MOVE(-1, 1, 0) PLX_MOVE(0, 1, 0) PLX_MOVE(1, 1, 0)
-            PLX_MOVE(-1, -1, 1) PLX_MOVE(0, -1, 1) PLX_MOVE(1, -1, 1)
-            PLX_MOVE(-1, 0, 1) PLX_MOVE(0, 0, 1) PLX_MOVE(1, 0, 1)
-            PLX_MOVE(-1, 1, 1) PLX_MOVE(0, 1, 1) PLX_MOVE(1, 1, 1)
-#undef PLX_MOVE
-            default: break;
-          }
+          move_by(dx, dy, dz, gs, gc);
         }
       }
     }
