@@ -646,6 +646,7 @@ def run_ours(args):
             "ms_per_step": rank_max(sum(recomp["step_ms"]), world, "cuda") / K,
             "kernels_ms": {"forward": statistics.mean(recomp["fwd_ms"]),
                            "backward_grid": statistics.mean(recomp["bwd_ms"])},
+            "launch_config": recomp["launch_config"],
             "note": "the same step without the sample cache: the adjoint re-marches every ray, "
                     "recomputing T_i and the prefix sums; the headline keeps "
                     f"{main['cache']['bytes'] / 1e9:.2f} GB of kept samples instead"},

@@ -415,7 +415,8 @@ plx_status plx_grid_grow(const plx_grid_desc *desc, int32_t *links,
  * of 2 cells per axis), per kernel: bit 0 forward, 1 grid adjoint, 2 pose
  * Jacobian, 3 batched launch (PLX_FINE_*). *_blocks: each ray kernel is compiled for 1 or 2
  * resident blocks of 256 threads per SM (a register budget of 255 or 128 per
- * thread): forward, grid adjoint, pose Jacobian, batched launch. Defaults are
+ * thread): forward, grid adjoint, pose Jacobian, batched launch; the forward
+ * also for 3 (80 registers). Defaults are
  * the best measured on B300 for room-scale grids; the Python autotuner times
  * the alternatives on a caller's workload. */
 #define PLX_FINE_FORWARD 1

@@ -3,7 +3,7 @@
 The choices are those of ``plx_grid_set_config``: the granularity of the
 empty-space map (blocks of 2^shift cells per axis) and, per ray kernel, the
 number of resident 256-thread blocks per SM it is compiled for (1 or 2: a
-register budget of 255 or 128 per thread). None of them changes a result; they
+register budget of 255 or 128 per thread; the forward also 3, 80 registers). None of them changes a result; they
 trade occupancy against spills and skipping granularity against lookup cost,
 and the best values depend on the grid and the rays, and on the options: with
 options naming a sample cache, tune_mapping times the cached adjoint. The tuner times the
@@ -28,6 +28,7 @@ def _fine(bit):
     """Candidates of fine_skip that toggle one kernel's bit."""
     return lambda cur: [cur | bit, cur & ~bit]
 BLOCKS = (1, 2)
+FORWARD_BLOCKS = (1, 2, 3)
 
 
 def _cache_path(path=None):
@@ -110,7 +111,8 @@ def tune_mapping(grid, cams, opts, rgb_target, depth_target, rays=None, reps=3, 
     """Tune block_shift, fine_skip, forward_blocks and adjoint_blocks on one mapping step
     (forward + adjoint) of these rays. Returns dict(config, ms, trials)."""
     n = cams.n_pixels() if rays is None else int(rays[1].shape[0])
-    key = _key(grid, "mapping", n)
+    # with a sample cache another adjoint kernel runs: its own entry
+    key = _key(grid, "mapping+cache" if opts.sample_cap > 0 else "mapping", n)
     if use_cache:
         hit = _lookup(grid, key, cache)
         if hit:
@@ -127,7 +129,7 @@ def tune_mapping(grid, cams, opts, rgb_target, depth_target, rays=None, reps=3, 
     log = []
     cfg, ms = _descend(grid, step, [("block_shift", SHIFTS), ("fine_skip", _fine(FINE_FORWARD)),
                                     ("fine_skip", _fine(FINE_ADJOINT)), ("adjoint_blocks", BLOCKS),
-                                    ("forward_blocks", BLOCKS)], reps, log)
+                                    ("forward_blocks", FORWARD_BLOCKS)], reps, log)
     entry = {"config": cfg, "ms": ms, "trials": [[c, t] for c, t in log]}
     _store(key, entry, cache)
     return dict(entry, cached=False)

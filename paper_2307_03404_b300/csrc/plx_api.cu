@@ -646,8 +646,10 @@ extern "C" plx_status plx_grid_set_config(plx_grid* g, const plx_launch_config* 
   if (!g || !c) return fail(PLX_EINVAL, "%s: null argument", what);
   if (c->block_shift < 1 || c->block_shift > 6)
     return fail(PLX_EINVAL, "%s: block_shift %d out of [1, 6]", what, c->block_shift);
-  const int v[4] = {c->forward_blocks, c->adjoint_blocks, c->pose_blocks, c->batch_blocks};
-  for (int i = 0; i < 4; ++i)
+  if (c->forward_blocks < 1 || c->forward_blocks > 3)
+    return fail(PLX_EINVAL, "%s: forward blocks per SM must be 1, 2 or 3", what);
+  const int v[3] = {c->adjoint_blocks, c->pose_blocks, c->batch_blocks};
+  for (int i = 0; i < 3; ++i)
     if (v[i] != 1 && v[i] != 2)
       return fail(PLX_EINVAL, "%s: blocks per SM must be 1 or 2", what);
   if (c->fine_skip < 0 || c->fine_skip > 15)

@@ -45,6 +45,22 @@ constexpr int kRecordSlots = 32;      // record = 32 slots (28 used)
     }                                                             \
   } while (0)
 
+// The same with a third choice, 3 blocks per SM (a register budget of 80):
+// the forward, whose 16-bit storage modes spill little there.
+#define PLX_DISPATCH_SM3(store, minb, CALL)                        \
+  do {                                                            \
+    if ((minb) >= 3) {                                            \
+      switch (store) {                                            \
+        case PLX_STORE_F32: CALL(PLX_STORE_F32, 3); break;        \
+        case PLX_STORE_BF16: CALL(PLX_STORE_BF16, 3); break;      \
+        case PLX_STORE_F16: CALL(PLX_STORE_F16, 3); break;        \
+        default: CALL(PLX_STORE_F32_BF16, 3); break;              \
+      }                                                           \
+    } else {                                                      \
+      PLX_DISPATCH_SM(store, minb, CALL);                         \
+    }                                                             \
+  } while (0)
+
 // ---------------------------------------------------------------- params
 struct CamParam {
   float2 inv_fx, inv_fy, cx, cy;  // 1/fx, 1/fy, principal point as (hi, lo) float pairs

@@ -304,7 +304,7 @@ void launch_forward(int store, int minb, const Common& P, float* rgb, float* dep
     k_forward<S, true, M><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts);  \
   else                                                                              \
     k_forward<S, false, M><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts)
-  PLX_DISPATCH_SM(store, minb, PLX_FWD);
+  PLX_DISPATCH_SM3(store, minb, PLX_FWD);
 #undef PLX_FWD
 }
 

@@ -38,8 +38,16 @@ def test_every_launch_config_gives_the_oracle_result():
             assert norm_err(H, rp.H) <= 1e-4 and norm_err(b, rp.b) <= 1e-4
     with pytest.raises(plx.PlxError):
         case.grid.set_config(block_shift=0)
+    # the forward also at 3 blocks per SM
+    case.grid.set_config(block_shift=3, forward_blocks=3, adjoint_blocks=2, pose_blocks=2,
+                         fine_skip=14)
+    got = case.forward(opts)
+    assert rel_err(got["rgb"], ref.rgb) <= 1e-5
+    np.testing.assert_array_equal(got["counts"][:, 1], ref.n_alloc)
     with pytest.raises(plx.PlxError):
         case.grid.set_config(adjoint_blocks=3)
+    with pytest.raises(plx.PlxError):
+        case.grid.set_config(forward_blocks=4)
     with pytest.raises(plx.PlxError):
         case.grid.set_config(fine_skip=16)
 
