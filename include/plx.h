@@ -287,14 +287,23 @@ plx_status plx_render_backward_pose(const plx_grid *grid,
  * that first call before any stream capture. All calls share the array, and
  * each call clears its counters on its own stream first: calls that overlap
  * on the GPU (several streams or host threads) race and return wrong sums.
- * Pixel-list entries out of range are skipped and do not count in M. Nothing
- * is allocated or freed. */
+ * Pixel-list entries out of range are skipped and do not count in M
+ * (plx_noalloc_error reports them). Nothing is allocated or freed. */
 plx_status plx_render_backward_pose_noalloc(
     const plx_grid_desc *desc, const int32_t *links, const void *records,
     const plx_cameras *cams, int32_t cam, const plx_rays *rays,
     const plx_render_opts *opts, const float *rgb_target,
     const float *depth_target, double *JtWJ, double *JtWr, double *loss,
     void *stream);
+
+/* The error word of the last plx_render_backward_pose_noalloc call on the
+ * current device, copied on `stream` into err_out (DEVICE or HOST int32 [1];
+ * nothing is allocated): 0, or bit 0 set when the pixel list held entries
+ * out of range (skipped, not counted in M). Enqueue it on the call's stream
+ * before the next call clears the word; calls that overlap race as described
+ * above. Errors: PLX_EINVAL (null err_out, or no call on this device yet),
+ * PLX_EUNSUPPORTED, PLX_ECUDA. */
+plx_status plx_noalloc_error(int32_t *err_out, void *stream);
 
 /* Sec. 5.3 (the pose is optimised directly). Gauss-Newton step, on the
  * device in FP64: solves (JtWJ + damping I) xi = -JtWr by Cholesky and sets

@@ -932,6 +932,28 @@ extern "C" plx_status plx_render_backward_pose_noalloc(
   return launch_check(what);
 }
 
+extern "C" plx_status plx_noalloc_error(int32_t* err_out, void* stream) {
+  const char* what = "noalloc_error";
+  if (!err_out) return fail(PLX_EINVAL, "%s: null err_out", what);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PLX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  if (dev < 0 || dev >= PLX_NOALLOC_MAX_DEVICES)
+    return fail(PLX_EUNSUPPORTED, "%s: device %d beyond %d", what, dev, PLX_NOALLOC_MAX_DEVICES);
+  char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    scratch = g_noalloc_ptr[dev];
+  }
+  if (!scratch)
+    return fail(PLX_EINVAL, "%s: no render_backward_pose_noalloc call on device %d yet", what,
+                dev);
+  Workspace* ws = reinterpret_cast<Workspace*>(scratch);
+  e = cudaMemcpyAsync(err_out, &ws->err, sizeof(int32_t), cudaMemcpyDefault, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(PLX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return PLX_OK;
+}
+
 // ------------------------------------------------------------ ceilings probe
 extern "C" plx_status plx_probe(int32_t kind, float* buf, int64_t n_rows, int32_t group,
                                 int32_t ops, int32_t blocks, void* stream) {

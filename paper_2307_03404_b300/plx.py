@@ -84,7 +84,7 @@ SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload"
            "plx_grid_check", "plx_render_backward_pose_noalloc", "plx_render_batch",
            "plx_grid_rmsprop", "plx_track_adam_step", "plx_grid_get_config",
            "plx_grid_set_config", "plx_grid_grow", "plx_pose_step_lm", "plx_sample_cache_bytes",
-           "plx_probe"]
+           "plx_probe", "plx_noalloc_error"]
 
 
 def _load():
@@ -119,6 +119,7 @@ def _load():
         "plx_pose_step_lm": [P, P, P, P, D, D, P, P, P, P],
         "plx_grid_grow": [C.POINTER(GridDesc), P, C.POINTER(Cameras), P, I32, D, P, P],
         "plx_probe": [I32, P, I64, I32, I32, I32, P],
+        "plx_noalloc_error": [P, P],
         "plx_render_backward_pose_noalloc": [C.POINTER(GridDesc), P, P, C.POINTER(Cameras), I32,
                                              C.POINTER(Rays), C.POINTER(RenderOpts), P, P, P, P,
                                              P, P],

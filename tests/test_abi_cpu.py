@@ -239,6 +239,14 @@ def test_probe_argument_errors(lib):
     assert b"kind" in lib.plx_last_error()
 
 
+def test_noalloc_error_checks_its_argument(lib):
+    """plx_noalloc_error rejects a null destination before touching a device."""
+    from paper_2307_03404_b300 import plx
+
+    assert plx._lib.plx_noalloc_error(None, None) == 1
+    assert b"err_out" in plx._lib.plx_last_error()
+
+
 def test_sample_cache_options_keep_the_cache_alive():
     """Options made by SampleCache.opts hold the cache: a temporary cache's
     device buffer is not freed (and reused) while the options live."""

@@ -10,7 +10,8 @@ entry's H, b and loss are compared with ``plx_render_backward_pose`` on a grid
 handle of the same storage and with the FP64 oracle on the same (rounded)
 values, on two calls in a row, in dense and list mode (with out-of-range
 pixels, which the entry skips and leaves out of M) and with the SH
-view-direction term. Free device memory and the torch allocator's reserved
+view-direction term, and the call's error word read back with
+``plx_noalloc_error``. Free device memory and the torch allocator's reserved
 bytes must not change across the calls. This file is collected last so that
 a run stopping at the first failure has run every other test; it also passes
 alone in a fresh process.
@@ -146,6 +147,8 @@ def test_noalloc_pose_matches_regular_entry_and_oracle_twice_in_a_row(scene, sto
     # the first call on a device finds the scratch array's address; from then
     # on a call touches no allocator at all
     noalloc(desc, links, records, cams, rays, o, rgb_t, depth_t)
+    err = torch.empty(1, dtype=torch.int32, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
     for call in range(2):
         H, b, loss = noalloc(desc, links, records, cams, rays, o, rgb_t, depth_t)
@@ -154,5 +157,10 @@ def test_noalloc_pose_matches_regular_entry_and_oracle_twice_in_a_row(scene, sto
         assert _norm_err(H, H_ref) <= 1e-4 and _norm_err(b, b_ref) <= 1e-4, call
         assert abs(loss[0] - rp.loss) <= 1e-5 * rp.loss, call
         assert _norm_err(H, rp.H) <= 1e-4 and _norm_err(b, rp.b) <= 1e-4, call
+        # the call's error word: bit 0 for the out-of-range list entries
+        err.fill_(-1)
+        assert plx._lib.plx_noalloc_error(C.c_void_p(err.data_ptr()), stream) == 0
+        torch.cuda.synchronize()
+        assert int(err.item()) == (1 if mode == "list" else 0), call
     assert torch.cuda.mem_get_info()[0] == free0
     assert torch.cuda.memory_reserved() == reserved0
