@@ -31,16 +31,24 @@ def test_short_sequence_maps_and_tracks():
 
 def test_benched_sequence_tracks_to_its_end():
     """The benchmark's pipeline: 300 frames of 640x480 along 3.9 m of the
-    256^3 room, every 10th frame and the last one mapped, every frame
-    tracked with Adam and with Levenberg-Marquardt. The frames after the
-    last mapped one used to drift to 23 cm (they see space no keyframe
-    observed); with the last frame mapped no frame ends more than a few
-    centimetres off."""
+    256^3 room, every 10th frame and the last one mapped (3000 RMSProp
+    steps), every frame tracked with Adam and with Levenberg-Marquardt. The
+    frames after the last mapped one used to drift to 23 cm (they see space
+    no keyframe observed); with the last frame mapped no frame ends more
+    than a few centimetres off.
+
+    The last 50 frames look at surfaces about 4 m away, which the map fits
+    last: their error is the map's, not accumulated drift. A late frame
+    tracked on its own from its true pose ends where the sequential tracker
+    put it, and the error of those frames shrinks with mapping steps (mean
+    1.85 cm after 1000 steps, 0.7 cm after 3000)."""
     R, occ, npr, seed = scenes.WORKLOADS["room256"]
     sc = scenes.room_scene(R, occ, npr, seed)
+    keep = {}
     out = pipeline.run(sc, per_frame=True,
-                       extra_track_cfgs=[pipeline.TrackConfig(method="lm", lm_iters=10)])
-    assert out["keyframes"] == 31
+                       extra_track_cfgs=[pipeline.TrackConfig(method="lm", lm_iters=10)],
+                       keep=keep)
+    assert out["keyframes"] == 31 and out["map_steps"] == 3000
     # the mapping's sample cache is watched and re-sized: after the last
     # re-sizing at most 1% of a step's rays overflow it and re-march
     log = out["sample_cache"]
@@ -49,7 +57,17 @@ def test_benched_sequence_tracks_to_its_end():
     assert log["overflow"] and max(after, default=0) <= 0.01 * out["map_rays_per_step"]
     for res in (out, out["other_trackers"][0]):
         err = np.array(res["err_m"])
-        assert res["median_err_m"] < 0.006, res["median_err_m"]
-        assert res["ate_m"] < 0.015, res["ate_m"]
-        assert err.max() < 0.06, (int(err.argmax()), float(err.max()))
-        assert err[-10:].max() < 0.06
+        assert res["median_err_m"] < 0.004, res["median_err_m"]
+        assert res["ate_m"] < 0.009, res["ate_m"]
+        assert err.max() < 0.04, (int(err.argmax()), float(err.max()))
+        assert err[250:].mean() < 0.012, float(err[250:].mean())
+    # frame 285, tracked alone from its true pose with the same LM tracker,
+    # lands within a few millimetres of the sequential estimate
+    k = 285
+    cams, rgb, depth, gt = keep["cams"], keep["rgb"], keep["depth"], keep["gt"]
+    est, _ = pipeline.track_sequence(keep["grid"], [cams[k]], rgb[k:k + 1], depth[k:k + 1],
+                                     keep["opts"], pipeline.TrackConfig(method="lm", lm_iters=10))
+    alone = float(np.linalg.norm(est[0][:, 3] - gt[k][:, 3]))
+    seq = out["other_trackers"][0]["err_m"][k]
+    assert abs(alone - seq) < 0.004, (alone, seq)
+    keep["close"]()
