@@ -121,12 +121,13 @@ def measured_traffic(kernel, workload, storage, n_rays=None, key="dram_bytes_per
     return _per_launch(rec, key, n_rays) if rec and key in rec else None
 
 
-def issue_roofline(kernel, ms, storage, clocks, n_rays=None, workload="room256"):
+def issue_roofline(kernel, ms, storage, clocks, n_rays=None, workload="room256", ceil=None):
     """Instruction-issue utilisation of a kernel: warp instructions per launch
     (ncu, profiles/traffic.json, valid for the current sources, scaled to
-    n_rays rays) over the live launch time, against one warp instruction per
-    clock per SM sub-partition (4 per SM) at the SM clock sampled during the
-    run."""
+    n_rays rays) over the live launch time, against the issue rate plx_probe
+    measures live (independent FP32 FMA chains, ``ceil["issue_warp_inst_per_s"]``);
+    without that measurement, against one warp instruction per clock per SM
+    sub-partition (4 per SM) at the SM clock sampled during the run."""
     import torch
 
     rec = measured_profile(kernel, workload, storage)
@@ -134,12 +135,17 @@ def issue_roofline(kernel, ms, storage, clocks, n_rays=None, workload="room256")
         return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2032.0
-    peak = sms * 4 * mhz * 1e6
+    nominal = sms * 4 * mhz * 1e6
+    measured = (ceil or {}).get("issue_warp_inst_per_s")
+    peak = measured or nominal
     wi = _per_launch(rec, "warp_instructions_per_launch", n_rays)
     achieved = wi / (ms / 1e3)
+    basis = (f"measured: plx_probe FP32 FMA issue rate ({measured / nominal:.3f} of {sms} SMs x "
+             f"4 sub-partitions x 1 warp instruction per clock x {mhz:.0f} MHz)" if measured else
+             f"{sms} SMs x 4 sub-partitions x 1 warp instruction per clock x {mhz:.0f} MHz")
     return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s",
             "frac": achieved / peak, "warp_instructions_per_launch": wi,
-            "peak_basis": f"{sms} SMs x 4 sub-partitions x 1 warp instruction per clock x {mhz:.0f} MHz"}
+            "nominal_peak": nominal, "peak_basis": basis}
 
 
 def l2_ceilings(rows=600_000, reps=5):
@@ -176,14 +182,38 @@ def l2_ceilings(rows=600_000, reps=5):
             ms = e0.elapsed_time(e1) / reps
             best = max(best, blocks * 256 * ops * per / (ms / 1e3))
         out[name] = best
+    # instruction issue: 512 FMAs per thread and operation, no memory traffic
+    # (the few loop instructions per 512 FMAs are not counted: ncu counts
+    # 1.024 instructions per FMA with 128 FMAs per operation)
+    # (about 20 ms of warm-up first: a lone launch of a few hundred us right
+    # after other work read as low as 0.8 of the rate it settles at)
+    best = 0.0
+    for bps in (8, 16):
+        blocks, ops = bps * sms, 64
+        for _ in range(40):
+            plx.probe(plx.PROBE_ISSUE, buf, 1, ops, blocks)
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                plx.probe(plx.PROBE_ISSUE, buf, 1, ops, blocks)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            best = max(best, blocks * 256 // 32 * ops * 512 / (ms / 1e3))
+    out["issue"] = best
     del buf
     return {"red_per_s": out["red"], "red_rows_per_s": out["red_rows"],
-            "gather_float4_per_s": out["gather"], "buffer_MB": rows * 128 / 1e6,
+            "gather_float4_per_s": out["gather"], "issue_warp_inst_per_s": out["issue"],
+            "buffer_MB": rows * 128 / 1e6,
             "how": "plx_probe: each lane 32 times picks a random 128-byte row of the buffer and "
                    "issues 7 float4 atomic adds (red, per float4) or 7 float4 loads (gather); "
                    "red_rows: the same rows and adds, 7 lanes per row with one float4 each "
-                   "(one coalesced request per row, per row); best of 8 and 16 blocks of 256 "
-                   "threads per SM, CUDA events over 5 launches"}
+                   "(one coalesced request per row, per row); issue: 512 independent FP32 FMAs "
+                   "per thread and operation, counted as warp instructions, after 40 warm-up "
+                   "launches, best of 3; best of 8 and 16 blocks of 256 threads per SM, CUDA "
+                   "events over 5 launches"}
 
 
 # how each adjoint kernel sends a corner's 7 float4 reductions: per lane (7 L2
@@ -240,7 +270,7 @@ def roofline_block(kernel, workload, storage, n_rays, ms, ceil, compulsory, no_r
                  "allocated corner per gather, 1792 B of FP32 gradient read-modify-write per "
                  "such sample in the adjoint, per-ray I/O); frac > 1 means L1/L2 reuse, not HBM "
                  "use"}
-    issue = issue_roofline(kernel, ms, storage, clocks, n_rays, workload)
+    issue = issue_roofline(kernel, ms, storage, clocks, n_rays, workload, ceil)
     cands = dict(l2 or {})
     if issue:
         cands["issue"] = issue
@@ -257,8 +287,8 @@ def roofline_block(kernel, workload, storage, n_rays, ms, ceil, compulsory, no_r
                                "live for the same access (float4 reductions, per lane or "
                                "coalesced per row as the kernel sends them, or gathers of "
                                "random 128-byte rows in L2), and warp instructions against "
-                               "one per clock per SM sub-partition at the sampled clock "
-                               "(alu); bound = the largest of these fractions"})
+                               "the issue rate plx_probe measures live for independent FP32 "
+                               "FMAs (alu); bound = the largest of these fractions"})
     else:
         block.update({"bound": "hbm", "achieved": comp_gbs, "peak": hbm, "unit": "GB/s",
                       "frac": comp_gbs / hbm, "hbm": hb,

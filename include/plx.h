@@ -503,6 +503,14 @@ plx_status plx_render_batch(const plx_grid *grid, const plx_cameras *cams,
  *                     instruction covers 4 rows, 7 lanes per row with one
  *                     float4 each (one coalesced request per row);
  *                     ops * threads rows per launch ('group' is ignored)
+ *   PLX_PROBE_ISSUE   instruction issue instead of memory: each thread, `ops`
+ *                     times, 512 FP32 fused multiply-adds in 8 independent
+ *                     chains (64 per chain), so the SM sub-partitions issue
+ *                     back to back; 512 * ops * threads / 32 warp FMA
+ *                     instructions per launch (plus a few per `ops` round
+ *                     for the loop). buf is written only if a chain ends at
+ *                     a value the finite inputs cannot reach ('group' and
+ *                     n_rows >= 1 as above, otherwise unused)
  *   buf     DEVICE float [n_rows][PLX_GRAD_STRIDE], 16-byte aligned, holding
  *           finite values (RED adds to them); 1 <= n_rows < 2^32
  *   blocks  thread blocks of 256 threads (1 .. 2^20); ops 1 .. 1024;
@@ -512,6 +520,7 @@ plx_status plx_render_batch(const plx_grid *grid, const plx_cameras *cams,
 #define PLX_PROBE_GATHER 1
 #define PLX_PROBE_STREAM 2
 #define PLX_PROBE_RED_ROWS 3
+#define PLX_PROBE_ISSUE 4
 plx_status plx_probe(int32_t kind, float *buf, int64_t n_rows, int32_t group,
                      int32_t ops, int32_t blocks, void *stream);
 

@@ -959,7 +959,7 @@ extern "C" plx_status plx_probe(int32_t kind, float* buf, int64_t n_rows, int32_
                                 int32_t ops, int32_t blocks, void* stream) {
   const char* what = "plx_probe";
   if (kind != PLX_PROBE_RED && kind != PLX_PROBE_GATHER && kind != PLX_PROBE_STREAM &&
-      kind != PLX_PROBE_RED_ROWS)
+      kind != PLX_PROBE_RED_ROWS && kind != PLX_PROBE_ISSUE)
     return fail(PLX_EINVAL, "%s: unknown kind %d", what, kind);
   if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15) != 0)
     return fail(PLX_EINVAL, "%s: buffer null or not 16-byte aligned", what);

@@ -15,6 +15,10 @@
 //                     float4 sent by 7 lanes at once (lanes 8g..8g+6 of a
 //                     warp instruction cover row g of 4), as the sample-cache
 //                     adjoint's warp-cooperative scatter sends them.
+//   PLX_PROBE_ISSUE   independent FP32 FMA chains and no memory traffic: the
+//                     rate at which the SM sub-partitions issue warp
+//                     instructions, the ceiling of the forward and the pose
+//                     kernel, whose time goes to instruction issue.
 // Every access stays inside [buf, buf + n_rows * 128 bytes): rows are drawn as
 // (hash * n_rows) >> 32 < n_rows and the stream walks indices below n_rows * 8.
 #include "plx_internal.cuh"
@@ -99,12 +103,34 @@ k_probe_stream(float* __restrict__ buf, uint32_t n_rows, int ops) {
   if (acc == -1.2345e38f) buf[0] = acc;
 }
 
+__global__ void __launch_bounds__(256)
+k_probe_issue(float* __restrict__ buf, uint32_t n_rows, int ops) {
+  // multiplier and addend from the arguments, so nothing folds at compile time
+  const float a = 1.0f - 1.0e-7f * (float)(n_rows & 7u), b = 1.0e-7f;
+  float x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = (float)(threadIdx.x + c);
+  for (int it = 0; it < ops; ++it) {
+#pragma unroll
+    for (int u = 0; u < 64; ++u)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) x[c] = fmaf(x[c], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  // |x| stays below 300 for finite inputs: the store never happens, but the
+  // compiler cannot drop the chains
+  if (s == -1.2345e38f) buf[0] = s;
+}
+
 void launch_probe(int kind, float* buf, uint32_t n_rows, int group, int ops, int blocks,
                   cudaStream_t s) {
   switch (kind) {
     case PLX_PROBE_RED: k_probe_red<<<blocks, 256, 0, s>>>(buf, n_rows, group, ops); break;
     case PLX_PROBE_GATHER: k_probe_gather<<<blocks, 256, 0, s>>>(buf, n_rows, group, ops); break;
     case PLX_PROBE_RED_ROWS: k_probe_red_rows<<<blocks, 256, 0, s>>>(buf, n_rows, ops); break;
+    case PLX_PROBE_ISSUE: k_probe_issue<<<blocks, 256, 0, s>>>(buf, n_rows, ops); break;
     default: k_probe_stream<<<blocks, 256, 0, s>>>(buf, n_rows, ops); break;
   }
 }

@@ -562,7 +562,7 @@ def track_adam_step(grid: Grid, cams: CameraSet, cam: int, opts, n_rays, seed, r
     return out
 
 
-PROBE_RED, PROBE_GATHER, PROBE_STREAM, PROBE_RED_ROWS = 0, 1, 2, 3
+PROBE_RED, PROBE_GATHER, PROBE_STREAM, PROBE_RED_ROWS, PROBE_ISSUE = 0, 1, 2, 3, 4
 
 
 def probe(kind, buf, group=1, ops=64, blocks=None, stream=None):

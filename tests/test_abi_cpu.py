@@ -235,7 +235,9 @@ def test_probe_argument_errors(lib):
     # the coalesced-row reductions ignore `group`
     assert lib.plx_probe(plx.PROBE_RED_ROWS, fake, 16, 99, 0, 1, None) == 1
     assert b"ops" in lib.plx_last_error()
-    assert lib.plx_probe(4, fake, 16, 1, 1, 1, None) == 1
+    assert lib.plx_probe(plx.PROBE_ISSUE, fake, 16, 1, 2000, 1, None) == 1
+    assert b"ops" in lib.plx_last_error()
+    assert lib.plx_probe(5, fake, 16, 1, 1, 1, None) == 1
     assert b"kind" in lib.plx_last_error()
 
 
