@@ -622,3 +622,54 @@ def test_room512_forward_and_pose_sampled_against_oracle(room512):
     assert ld[1] == acc_M
     assert norm_err(Hd * ld[1], acc_H) <= 1e-9
     assert norm_err(bd * ld[1], acc_b) <= 1e-9
+
+
+@pytest.mark.parametrize("cache_cap", [None, 64])
+def test_no_valid_target_depth(cache_cap):
+    """Degenerate targets: every depth missing (0, NaN or negative), so M = 0
+    rays enter the loss (Eq. 4-5, 11). The oracle then gives loss 0 and zero
+    gradients; the grid adjoint, the pose system and the batched launch must
+    agree (no division by M = 0), and a Gauss-Newton step on the zero system
+    reports it as not positive definite and leaves the pose alone."""
+    g = scenes.tiny_grid(7, seed=5, alloc_frac=0.7, sigma_mean=2.0, sigma_std=2.0)
+    cams = tiny_cams()
+    opts = dict(step=0.1, bg=(0.2, 0.1, 0.3), lambda_d=0.5)
+    case = GpuCase(g, cams)
+    n = case.cams.n_pixels()
+    rng = np.random.default_rng(3)
+    rgb_t = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    depth_t = np.zeros(n, np.float32)
+    depth_t[1::3] = np.nan
+    depth_t[2::3] = -1.0
+    ref = oracle.grad_grid(g, cams, opts, rgb_t, depth_t)
+    assert ref.M == 0 and ref.loss == 0.0
+    gd, gs, gpad, loss = case.backward_grid(opts, rgb_t, depth_t, cache_cap=cache_cap)
+    assert loss[0] == 0.0 and loss[1] == 0.0
+    assert not gd.any() and not gs.any() and not gpad.any()
+    w0 = cams[0].width * cams[0].height
+    H, b, ploss = case.backward_pose(opts, 0, rgb_t[:w0], depth_t[:w0])
+    rp = oracle.pose_jacobian(g, [cams[0]], opts, rgb_t[:w0], depth_t[:w0])
+    assert rp.M == 0 and not rp.H.any() and not rp.b.any()
+    assert not H.any() and not b.any() and ploss[0] == 0.0 and ploss[1] == 0.0
+    pose = case.cams.poses[0].clone()
+    st = torch.full((1,), 7, device="cuda", dtype=torch.int32)
+    plx.pose_step(dev(H, torch.float64), dev(b, torch.float64), pose, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 1
+    assert torch.equal(pose, case.cams.poses[0])
+    o = plx.opts_from_dict(opts)
+    if cache_cap is not None:
+        o = plx.SampleCache.for_batch(cache_cap).opts(o)
+    work = [(0, plx.WORK_MAP), (1, plx.WORK_TRACK), (1, plx.WORK_MAP)]
+    sizes = [cams[c].width * cams[c].height for c, _ in work]
+    rows = int(sum(sizes))
+    bt_rgb = rng.uniform(0, 1, (rows, 3)).astype(np.float32)
+    bt_depth = np.zeros(rows, np.float32)
+    grad, mloss, Hb, bb, tloss = plx.render_batch(case.grid, case.cams, work, o, dev(bt_rgb),
+                                                  dev(bt_depth))
+    torch.cuda.synchronize()
+    case.grid.check()
+    assert mloss.cpu().tolist() == [0.0, 0.0]
+    assert not grad.any().item()
+    assert not Hb.any().item() and not bb.any().item()
+    assert tloss.cpu().tolist() == [[0.0, 0.0]]
