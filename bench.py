@@ -928,16 +928,24 @@ def run_small_bench(args, barrier):
         plx.render_backward_pose(grid, cams, 0, opts, rgb_t, depth_t, out=pose_out)
 
     K = max(20, 10 * args.steps)
-    for _ in range(max(3, args.warmup)):
-        step()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(K):
-        step()
-    e1.record()
-    barrier()
-    ms = e0.elapsed_time(e1) / K
+
+    def timed():
+        for _ in range(max(3, args.warmup)):
+            step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            step()
+        e1.record()
+        barrier()
+        return e0.elapsed_time(e1) / K
+
+    ms = timed()  # default launch choices: a warp per ray at this size
+    config = grid.get_config()
+    grid.set_config(seg_rays=0)  # the same step with one ray per lane
+    ms_lane = timed()
+    grid.set_config(seg_rays=config["seg_rays"])
     cnt = plx.render_forward(grid, cams, opts, counts=True)["counts"].cpu().numpy()
     grid.close()
     return {"workload": "sphere64: dense 64^3 grid (262,144 vertices, FP32), one 64x48 frame "
@@ -945,6 +953,9 @@ def run_small_bench(args, barrier):
             "value": n_rays / (ms / 1e3), "unit": "rays/s", "ms_per_step": ms, "steps": K,
             "S_all_mean": float(cnt[:, 0].mean()), "S_occ_mean": float(cnt[:, 1].mean()),
             "loss": loss.cpu().tolist(), "gpu_launches_per_step": 4,
+            "launch_config": config,
+            "one_ray_per_lane": {"value": n_rays / (ms_lane / 1e3), "ms_per_step": ms_lane,
+                                 "launch": "seg_rays = 0: each lane marches a whole ray"},
             "timing": "K steps back to back between two CUDA events; the grid stays in L2"}
 
 

@@ -425,7 +425,13 @@ plx_status plx_grid_grow(const plx_grid_desc *desc, int32_t *links,
  * Jacobian, 3 batched launch (PLX_FINE_*). *_blocks: each ray kernel is compiled for 1 or 2
  * resident blocks of 256 threads per SM (a register budget of 255 or 128 per
  * thread): forward, grid adjoint, pose Jacobian, batched launch; the forward
- * also for 3 (80 registers). Defaults are
+ * also for 3 (80 registers). seg_rays: rays per warp. A call over at most
+ * seg_rays rays (ray slots: dense frames count whole 8x4 tiles) runs a warp
+ * per ray in the forward, the re-marching grid adjoint and the pose Jacobian
+ * (the 32 lanes split each ray's samples and a scan combines the segments;
+ * only without early stop, sample cache or view-direction term, and for the
+ * sigmoid colour), larger calls one ray per lane; 0 = always one ray per
+ * lane; at most 2^24. Defaults are
  * the best measured on B300 for room-scale grids; the Python autotuner times
  * the alternatives on a caller's workload. */
 #define PLX_FINE_FORWARD 1
@@ -440,6 +446,7 @@ typedef struct {
   int32_t pose_blocks;
   int32_t batch_blocks;
   int32_t fine_skip;
+  int32_t seg_rays;
 } plx_launch_config;
 
 /* Current launch choices of a grid (HOST out). */

@@ -1,9 +1,11 @@
 """Autotuner of the launch choices of a grid's kernels.
 
 The choices are those of ``plx_grid_set_config``: the granularity of the
-empty-space map (blocks of 2^shift cells per axis) and, per ray kernel, the
+empty-space map (blocks of 2^shift cells per axis), per ray kernel the
 number of resident 256-thread blocks per SM it is compiled for (1 or 2: a
-register budget of 255 or 128 per thread; the forward also 3, 80 registers). None of them changes a result; they
+register budget of 255 or 128 per thread; the forward also 3, 80 registers),
+and the rays per warp (one ray per lane, or a warp per ray up to
+``seg_rays`` rays). None of them changes a result; they
 trade occupancy against spills and skipping granularity against lookup cost,
 and the best values depend on the grid and the rays, and on the options: with
 options naming a sample cache, tune_mapping times the cached adjoint. The tuner times the
@@ -29,6 +31,12 @@ def _fine(bit):
     return lambda cur: [cur | bit, cur & ~bit]
 BLOCKS = (1, 2)
 FORWARD_BLOCKS = (1, 2, 3)
+# rays per warp (seg_rays): one ray per lane (0), or a warp per ray for calls
+# up to the default 16384 ray slots or up to 2^24; tried only for calls of at
+# most SEG_TUNE_MAX rays, where a warp per ray can win (above, the 32 lanes of
+# a warp splitting one ray cost more than they save)
+SEG_RAYS = (0, 16384, 1 << 24)
+SEG_TUNE_MAX = 1 << 16
 
 
 def _cache_path(path=None):
@@ -108,8 +116,9 @@ def _store(key, entry, cache):
 
 def tune_mapping(grid, cams, opts, rgb_target, depth_target, rays=None, reps=3, cache=None,
                  use_cache=True):
-    """Tune block_shift, fine_skip, forward_blocks and adjoint_blocks on one mapping step
-    (forward + adjoint) of these rays. Returns dict(config, ms, trials)."""
+    """Tune block_shift, fine_skip, forward_blocks and adjoint_blocks (and, for
+    few rays without a sample cache, seg_rays) on one mapping step (forward +
+    adjoint) of these rays. Returns dict(config, ms, trials)."""
     n = cams.n_pixels() if rays is None else int(rays[1].shape[0])
     # with a sample cache another adjoint kernel runs: its own entry
     key = _key(grid, "mapping+cache" if opts.sample_cap > 0 else "mapping", n)
@@ -127,9 +136,12 @@ def tune_mapping(grid, cams, opts, rgb_target, depth_target, rays=None, reps=3, 
                                  fw["depth"], rays=rays, grad=grad, loss=loss)
 
     log = []
-    cfg, ms = _descend(grid, step, [("block_shift", SHIFTS), ("fine_skip", _fine(FINE_FORWARD)),
-                                    ("fine_skip", _fine(FINE_ADJOINT)), ("adjoint_blocks", BLOCKS),
-                                    ("forward_blocks", FORWARD_BLOCKS)], reps, log)
+    fields = [("block_shift", SHIFTS), ("fine_skip", _fine(FINE_FORWARD)),
+              ("fine_skip", _fine(FINE_ADJOINT)), ("adjoint_blocks", BLOCKS),
+              ("forward_blocks", FORWARD_BLOCKS)]
+    if n <= SEG_TUNE_MAX and opts.sample_cap == 0:
+        fields.insert(0, ("seg_rays", SEG_RAYS))
+    cfg, ms = _descend(grid, step, fields, reps, log)
     entry = {"config": cfg, "ms": ms, "trials": [[c, t] for c, t in log]}
     _store(key, entry, cache)
     return dict(entry, cached=False)
@@ -137,8 +149,10 @@ def tune_mapping(grid, cams, opts, rgb_target, depth_target, rays=None, reps=3, 
 
 def tune_tracking(grid, cams, cam, opts, rgb_target, depth_target, reps=3, cache=None,
                   use_cache=True):
-    """Tune pose_blocks (and block_shift, fine_skip) on one pose-Jacobian launch."""
-    key = _key(grid, "tracking", cams.n_pixels(cam))
+    """Tune pose_blocks (and block_shift, fine_skip; seg_rays for few rays) on
+    one pose-Jacobian launch."""
+    n = cams.n_pixels(cam)
+    key = _key(grid, "tracking", n)
     if use_cache:
         hit = _lookup(grid, key, cache)
         if hit:
@@ -151,8 +165,10 @@ def tune_tracking(grid, cams, cam, opts, rgb_target, depth_target, reps=3, cache
         plx.render_backward_pose(grid, cams, cam, opts, rgb_target, depth_target, out=out)
 
     log = []
-    cfg, ms = _descend(grid, step, [("pose_blocks", BLOCKS), ("block_shift", SHIFTS),
-                                    ("fine_skip", _fine(FINE_POSE))], reps, log)
+    fields = [("pose_blocks", BLOCKS), ("block_shift", SHIFTS), ("fine_skip", _fine(FINE_POSE))]
+    if n <= SEG_TUNE_MAX:
+        fields.insert(0, ("seg_rays", SEG_RAYS))
+    cfg, ms = _descend(grid, step, fields, reps, log)
     entry = {"config": cfg, "ms": ms, "trials": [[c, t] for c, t in log]}
     _store(key, entry, cache)
     return dict(entry, cached=False)

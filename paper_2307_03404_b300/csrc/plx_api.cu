@@ -328,6 +328,7 @@ plx_status plx_grid_create(const plx_grid_desc* desc, const int32_t* links, cons
   g->cfg.pose_blocks = kDefaultPoseBlocks;
   g->cfg.batch_blocks = kDefaultBatchBlocks;
   g->cfg.fine_skip = kDefaultFineSkip;
+  g->cfg.seg_rays = kSegRays;
   apply_config(g);
   const size_t ws_bytes = sizeof(Workspace) +
                           ((size_t)g->max_pose_blocks + PLX_MAX_CAMERAS) * 32 * sizeof(double);
@@ -442,6 +443,7 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
   P.g.nbx = g->nb[0];
   P.g.nby = g->nb[1];
   P.g.blk_shift = g->cfg.block_shift;
+  P.g.seg_rays = g->cfg.seg_rays;
   P.g.fblk = (g->cfg.fine_skip & fine_bit) ? g->fblk : nullptr;
   P.g.fnbx = g->fnb[0];
   P.g.fnby = g->fnb[1];
@@ -654,6 +656,8 @@ extern "C" plx_status plx_grid_set_config(plx_grid* g, const plx_launch_config* 
       return fail(PLX_EINVAL, "%s: blocks per SM must be 1 or 2", what);
   if (c->fine_skip < 0 || c->fine_skip > 15)
     return fail(PLX_EINVAL, "%s: fine_skip must be a mask of PLX_FINE_* bits", what);
+  if (c->seg_rays < 0 || c->seg_rays > (1 << 24))
+    return fail(PLX_EINVAL, "%s: seg_rays %d out of [0, 2^24]", what, c->seg_rays);
   if (c->block_shift != g->cfg.block_shift || (c->fine_skip != 0) != (g->cfg.fine_skip != 0)) {
     const cudaError_t e =
         build_block_map(g, c->block_shift, c->fine_skip != 0, (cudaStream_t)stream);
@@ -915,6 +919,7 @@ extern "C" plx_status plx_render_backward_pose_noalloc(
   view.ws = scratch;
   view.cfg.block_shift = kDefaultBlkShift;  // unused: the view has no empty-space map
   view.cfg.fine_skip = 0;
+  view.cfg.seg_rays = kSegRays;
   for (int a = 0; a < 3; ++a) view.inv_h[a] = (double)(desc->res[a] - 1) / (desc->hi[a] - desc->lo[a]);
   Common P;
   st = build_common(what, &view, cams, rays, opts, cam, PLX_FINE_POSE, P);

@@ -113,8 +113,9 @@ constexpr int kDefaultBatchBlocks = 1;
 constexpr int kDefaultFineSkip = PLX_FINE_ADJOINT | PLX_FINE_POSE | PLX_FINE_BATCH;
 constexpr int kFineShift = 1;         // second-level empty-space blocks: 2^1 cells per axis
 constexpr int kMaxSortedRays = 8192;  // Adam tracking: random rays put in image order up to this
-constexpr int64_t kSegRays = 16384;   // a warp per ray up to this many rays (forward, grid
-                                      // adjoint without a sample cache, pose Jacobian)
+constexpr int32_t kSegRays = 16384;   // default seg_rays: a warp per ray up to this many rays
+                                      // (forward, grid adjoint without a sample cache, pose
+                                      // Jacobian)
 
 struct GridView {
   const int32_t* links;           // [rz][ry][rx]
@@ -125,6 +126,7 @@ struct GridView {
   int32_t n_alloc;
   int32_t nbx, nby;
   int32_t blk_shift;              // blocks of 2^blk_shift cells per axis
+  int32_t seg_rays;               // a warp per ray for calls of at most this many ray slots
   const uint8_t* fblk;            // second level: blocks of 2^3 cells (null: none)
   int32_t fnbx, fnby;
   double lo[3];                   // box of the vertices

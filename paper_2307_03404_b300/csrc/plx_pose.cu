@@ -249,7 +249,8 @@ void launch_backward_pose(int store, int minb, const Common& P, const float* rgb
   k_backward_pose<S, M, false, true><<<seg_blocks, kBlock, 0, s>>>(P, rgb_t, depth_t, partials, \
                                                                    retire, JtWJ, JtWr, loss)
   // few rays: a warp per ray (needs stop_T = 0; the paper's Jacobian only)
-  const bool seg = P.ct.n_tiles * 32 <= kSegRays && !(P.o.stop_T > 0.f) && !P.o.dir_term;
+  const bool seg =
+      P.ct.n_tiles * 32 <= (int64_t)P.g.seg_rays && !(P.o.stop_T > 0.f) && !P.o.dir_term;
   int64_t seg_want = (P.ct.n_tiles * 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (seg_want < 1) seg_want = 1;
   const unsigned seg_blocks = (unsigned)(seg_want < max_blocks ? seg_want : max_blocks);

@@ -274,7 +274,7 @@ k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict
 // can cancel to a colour near zero, where summing in the scan's order instead
 // of front to back costs about 1e-8 absolute, over 1e-5 of a 1e-3 floor.)
 static bool use_seg(const Common& P) {
-  return P.ct.n_tiles * 32 <= kSegRays && !(P.o.stop_T > 0.f) && P.o.ccap == 0 &&
+  return P.ct.n_tiles * 32 <= (int64_t)P.g.seg_rays && !(P.o.stop_T > 0.f) && P.o.ccap == 0 &&
          P.o.color_act == PLX_ACT_SIGMOID;
 }
 

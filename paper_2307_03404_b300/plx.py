@@ -67,7 +67,8 @@ WORK_MAP, WORK_TRACK = 0, 1
 class LaunchConfig(C.Structure):
     _fields_ = [("block_shift", C.c_int32), ("forward_blocks", C.c_int32),
                 ("adjoint_blocks", C.c_int32), ("pose_blocks", C.c_int32),
-                ("batch_blocks", C.c_int32), ("fine_skip", C.c_int32)]
+                ("batch_blocks", C.c_int32), ("fine_skip", C.c_int32),
+                ("seg_rays", C.c_int32)]
 
 
 class RenderOpts(C.Structure):
@@ -232,7 +233,8 @@ class Grid:
 
     def set_config(self, stream=None, **kw):
         """Change launch choices (block_shift, fine_skip, forward_blocks,
-        adjoint_blocks, pose_blocks, batch_blocks); results do not change."""
+        adjoint_blocks, pose_blocks, batch_blocks, seg_rays); results do not
+        change."""
         cur = self.get_config()
         unknown = set(kw) - set(cur)
         if unknown:
