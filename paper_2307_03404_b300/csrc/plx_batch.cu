@@ -77,7 +77,7 @@ k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = 0.f;
       if (id.valid && depth_valid(dz))
-        pose_ray_values<STORE, DIRT>(P, r, rgb_t + 3 * id.out, dz, v);
+        pose_ray_values<STORE, DIRT, true>(P, r, rgb_t + 3 * id.out, dz, v);
       acc += warp_reduce_scatter(v, lane);
     } else if (id.valid && M > 0 && depth_valid(dz)) {
       float Y[9];

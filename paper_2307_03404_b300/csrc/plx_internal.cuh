@@ -576,6 +576,15 @@ __device__ __forceinline__ int block_exit(const RayF& r, int ix, int iy, int iz,
   return kn > (float)k ? (kn < 2.0e9f ? (int)kn : 2000000000) : k + 1;
 }
 
+// The block's per-thread corner caches in shared memory (32 floats per thread):
+// one array per kernel, shared by every march that keeps its corners there
+// (the batched kernel's re-marching adjoint and pose Jacobian use the same
+// 32 KB; a thread runs one of them at a time and uses only its own column).
+__device__ __forceinline__ float* corner_cache_smem() {
+  __shared__ float cache[32 * kBlock];
+  return cache;
+}
+
 // Same as load_cell, with the corner cache in shared memory: slot s of the
 // calling thread is sc[s * kBlock] (s = 4c: density of corner c, 4c+1+ch: its
 // projected colour), so the lanes of a warp hit distinct banks.

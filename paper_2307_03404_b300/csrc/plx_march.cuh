@@ -286,8 +286,7 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
   int cx = -1, cy = -1, cz = -1;
   bool empty = true, dirty = false;
   int32_t l[8];
-  __shared__ float cache[32 * kBlock];  // corner cache in shared memory: frees 32 registers
-  float* sc = cache + threadIdx.x;
+  float* sc = corner_cache_smem() + threadIdx.x;  // corner cache in shared memory: frees 32 registers
   float gs[8], gc[8][3];
 #pragma unroll
   for (int c = 0; c < 8; ++c) clear_corner(gs[c], gc[c]);

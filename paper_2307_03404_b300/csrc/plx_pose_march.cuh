@@ -79,8 +79,7 @@ __device__ __forceinline__ void march_pose(const Common& P, const RayF& r, const
   float cs_r[SMEM ? 1 : 8], cc_r[SMEM ? 1 : 8][3];
   float* sc = nullptr;
   if constexpr (SMEM) {
-    __shared__ float pose_cache[32 * kBlock];
-    sc = pose_cache + threadIdx.x;
+    sc = corner_cache_smem() + threadIdx.x;
   }
   float S[3] = {0.f, 0.f, 0.f}, SD = 0.f;
   float Ac[DIRT ? 8 : 1][3];
