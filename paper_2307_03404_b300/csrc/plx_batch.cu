@@ -88,7 +88,8 @@ k_batch(const __grid_constant__ Common P, const float* __restrict__ rgb_t,
       // samples between its two marches (slots past the cache re-march)
       const int64_t cslot = (int64_t)blockIdx.x * kBlock + threadIdx.x;
       const int cap = cslot < P.o.cn ? P.o.ccap : 0;
-      const int kept = march_forward<STORE, false>(P, r, Y, C, D, T, n_all, n_occ, cslot, cap);
+      const int kept =
+          march_forward<STORE, false, false, true>(P, r, Y, C, D, T, n_all, n_occ, cslot, cap);
       const float Dt = P.o.depth_is_z ? dz * r.dc_norm : dz;
       float gC[3], e2 = 0.f;
 #pragma unroll

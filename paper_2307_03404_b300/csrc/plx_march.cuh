@@ -12,7 +12,11 @@ namespace plx {
 // (transmittance from 1, sums from 0, no background, no early stop, no
 // cache): the segment's local (T, C, D), combined across the lanes of a warp
 // by seg_scan.
-template <int STORE, bool COUNT, bool SEG = false>
+// SMEM: the cell's corners in the block's shared corner cache (this
+// thread's column of corner_cache_smem) instead of 32 registers: slower in
+// the forward kernel, but the batched kernel, whose paths compete for 128
+// registers, spills less.
+template <int STORE, bool COUNT, bool SEG = false, bool SMEM = false>
 __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, const float Y[9],
                                              float C[3], float& D, float& T, int& n_all,
                                              int& n_occ, int64_t out, int cap, int k0 = 0,
@@ -21,7 +25,9 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
   int cx = -1, cy = -1, cz = -1;
   bool empty = true;
   int32_t l[8];
-  float cs[8], cc[8][3];
+  float cs_r[SMEM ? 1 : 8], cc_r[SMEM ? 1 : 8][3];
+  float* sc = nullptr;
+  if constexpr (SMEM) sc = corner_cache_smem() + threadIdx.x;
   C[0] = C[1] = C[2] = 0.f;
   D = 0.f;
   T = 1.f;
@@ -44,7 +50,10 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
         k = block_exit(r, ix, iy, iz, k, esh) - 1;
         continue;
       }
-      empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs, cc);
+      if constexpr (SMEM)
+        empty = load_cell_smem<STORE>(P.g, ix, iy, iz, Y, l, sc);
+      else
+        empty = load_cell<STORE>(P.g, ix, iy, iz, Y, l, cs_r, cc_r);
     }
     if (COUNT) n_occ += empty ? 0 : 1;
     if (empty) continue;
@@ -52,14 +61,16 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
     corner_weights(fx, fy, fz, w);
     float sig = 0.f;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) sig = fmaf(w[c], cs[c], sig);
+    for (int c = 0; c < 8; ++c)
+      sig = fmaf(w[c], SMEM ? sc[(4 * c) * kBlock] : cs_r[SMEM ? 0 : c], sig);
     if (!(sig > 0.f)) continue;
     float col[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       float a = 0.f;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) a = fmaf(w[c], cc[c][ch], a);
+      for (int c = 0; c < 8; ++c)
+        a = fmaf(w[c], SMEM ? sc[(4 * c + 1 + ch) * kBlock] : cc_r[SMEM ? 0 : c][ch], a);
       float dact;
       col[ch] = activate(a, P.o.color_act, dact);
     }
