@@ -250,7 +250,7 @@ def roofline_block(kernel, workload, storage, n_rays, ms, ceil, compulsory, no_r
     reduction rate (the grid adjoint's scatter), the L2 gather rate (record
     gathers) or instruction issue (bound "alu": one warp instruction per
     clock per SM sub-partition); the HBM figure beside it uses the compulsory
-    bytes (what the kernel cannot avoid moving), and the survey's no-reuse
+    bytes (what the kernel cannot avoid moving), and the fixed no-reuse
     model stays only as a diagnostic."""
     hbm, peak_kind = peaks()
     comp_gbs = compulsory / (ms / 1e3) / 1e9
@@ -265,7 +265,7 @@ def roofline_block(kernel, workload, storage, n_rays, ms, ceil, compulsory, no_r
     nr = no_reuse_bytes / (ms / 1e3) / 1e9
     block["no_reuse"] = {
         "bytes_per_launch": no_reuse_bytes, "achieved": nr, "peak": hbm, "frac": nr / hbm,
-        "model": "a diagnostic, not a roofline: the survey's fixed no-reuse byte model (32 B of "
+        "model": "a diagnostic, not a roofline: the fixed no-reuse byte model (32 B of "
                  "links per marched sample, 896 B (f32) / 448 B (16-bit) per sample with an "
                  "allocated corner per gather, 1792 B of FP32 gradient read-modify-write per "
                  "such sample in the adjoint, per-ray I/O); frac > 1 means L1/L2 reuse, not HBM "
