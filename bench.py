@@ -248,8 +248,9 @@ def roofline_block(kernel, workload, storage, n_rays, ms, ceil, compulsory, no_r
     """The roofline object of a dominant kernel. When its ncu record exists
     the binding ceiling is whichever the kernel comes closest to: the L2
     reduction rate (the grid adjoint's scatter), the L2 gather rate (record
-    gathers) or instruction issue (bound "alu": one warp instruction per
-    clock per SM sub-partition); the HBM figure beside it uses the compulsory
+    gathers) or instruction issue (bound "alu": against the warp-instruction
+    rate plx_probe measures for independent FP32 FMAs); the HBM figure beside
+    it uses the compulsory
     bytes (what the kernel cannot avoid moving), and the fixed no-reuse
     model stays only as a diagnostic."""
     hbm, peak_kind = peaks()
