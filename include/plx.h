@@ -141,7 +141,26 @@ typedef struct {
   int32_t sample_cap;  /* K: samples kept per ray in sample_cache, >= 0 */
   int64_t sample_rays; /* n: rays the cache was sized for (its row stride),
                           >= the call's n_rays */
+  int32_t *ray_range;  /* DEVICE int32 [n_rays][2], or NULL: each ray's
+                          compositing range (below), written by
+                          plx_render_forward and read by the re-marching
+                          adjoint of plx_render_backward_grid (ignored by
+                          every other call) */
 } plx_render_opts;
+
+/* Compositing range (Sec. 5.2: the adjoint recomputes T_i and the prefix sums
+ * of Eq. 9-10 front to back). With opts->ray_range set, plx_render_forward
+ * writes for ray r (its output row) the sample index of its first sample with
+ * sigma > 0 at [r][0] and one past its last at [r][1] (0, 0 when it has none),
+ * and plx_render_backward_grid re-marches each ray only over that range. No
+ * sample outside it composites, so where the range starts T = 1 and the
+ * prefix sums are 0, and the gradients are those of the full re-march (the
+ * same products; only the order of the atomic sums differs). It is the
+ * per-ray state a recomputing adjoint keeps (8 bytes per ray), and it also
+ * shortens the re-march of rays that overflow a sample cache. The adjoint
+ * call must name the same array, grid contents, cameras, rays and opts as the
+ * forward that wrote it (nothing checks this). With it, calls of at most
+ * seg_rays rays also run one ray per lane (plx_launch_config). */
 
 /* Sample cache (Sec. 5.2: what the adjoint of Eq. 8-10 needs per sample).
  * With opts->sample_cache set and opts->sample_cap = K > 0, plx_render_forward

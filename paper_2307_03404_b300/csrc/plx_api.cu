@@ -531,6 +531,16 @@ static plx_status build_common(const char* what, const plx_grid* g, const plx_ca
 // The sample cache of opts, laid out for n = sample_rays rows: float4 [K][n],
 // int32 [K][n], int32 [n]. Rows are rays (forward and grid adjoint: n must
 // cover the call's rays) or, with per_ray false, thread slots (batched launch).
+// The compositing range of plx_render_forward / plx_render_backward_grid
+// (every other call leaves P.o.range null).
+static plx_status set_ray_range(const char* what, const plx_render_opts* o, Common& P) {
+  if (!o->ray_range) return PLX_OK;
+  if (reinterpret_cast<uintptr_t>(o->ray_range) % 8 != 0)
+    return fail(PLX_EINVAL, "%s: ray_range must be 8-byte aligned", what);
+  P.o.range = reinterpret_cast<int2*>(o->ray_range);
+  return PLX_OK;
+}
+
 static plx_status set_sample_cache(const char* what, const plx_render_opts* o, Common& P,
                                    bool per_ray = true) {
   if (!o->sample_cache || o->sample_cap == 0) return PLX_OK;
@@ -564,6 +574,7 @@ plx_status plx_render_forward(const plx_grid* g, const plx_cameras* cams, const 
   Common P;
   plx_status st = build_common("render_forward", g, cams, rays, opts, -1, PLX_FINE_FORWARD, P);
   if (st == PLX_OK) st = set_sample_cache("render_forward", opts, P);
+  if (st == PLX_OK) st = set_ray_range("render_forward", opts, P);
   if (st != PLX_OK) return st;
   if (P.ct.n_rays > 0 && (!rgb_out || !depth_out))
     return fail(PLX_EINVAL, "render_forward: null rgb_out or depth_out");
@@ -580,6 +591,7 @@ plx_status plx_render_backward_grid(const plx_grid* g, const plx_cameras* cams,
   Common P;
   plx_status st = build_common("render_backward_grid", g, cams, rays, opts, -1, PLX_FINE_ADJOINT, P);
   if (st == PLX_OK) st = set_sample_cache("render_backward_grid", opts, P);
+  if (st == PLX_OK) st = set_ray_range("render_backward_grid", opts, P);
   if (st != PLX_OK) return st;
   if (P.ct.n_rays > 0 && (!rgb_target || !depth_target || !rgb || !depth))
     return fail(PLX_EINVAL, "render_backward_grid: null array argument");

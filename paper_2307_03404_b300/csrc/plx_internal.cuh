@@ -155,6 +155,8 @@ struct Opts {
   int32_t* ccount;                // [cn] samples with sigma > 0 per ray
   int64_t cn;                     // rays of the call
   int32_t ccap;                   // K
+  int2* range;                    // [n_rays] first and one past the last compositing
+                                  // sample of each ray (null: off)
 };
 
 struct Common {

@@ -16,7 +16,9 @@ namespace plx {
 // thread's column of corner_cache_smem) instead of 32 registers: slower in
 // the forward kernel, but the batched kernel, whose paths compete for 128
 // registers, spills less.
-template <int STORE, bool COUNT, bool SEG = false, bool SMEM = false>
+// RANGE: also write the ray's compositing range (first sample with
+// sigma > 0, one past the last; 0, 0 when none) to P.o.range[out].
+template <int STORE, bool COUNT, bool SEG = false, bool SMEM = false, bool RANGE = false>
 __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, const float Y[9],
                                              float C[3], float& D, float& T, int& n_all,
                                              int& n_occ, int64_t out, int cap, int k0 = 0,
@@ -33,6 +35,7 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
   T = 1.f;
   n_all = r.n;
   int kept = 0;
+  int rfirst = -1, rlast = -1;
   if constexpr (SEG) cap = 0;
   const int k_end = SEG ? k1 : r.n;
   for (int k = SEG ? k0 : 0; k < k_end; ++k) {
@@ -74,6 +77,10 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
       float dact;
       col[ch] = activate(a, P.o.color_act, dact);
     }
+    if constexpr (RANGE) {
+      if (rfirst < 0) rfirst = k;
+      rlast = k;
+    }
     if (cap > 0) {
       if (kept < cap) {
         const int64_t at = (int64_t)kept * P.o.cn + out;
@@ -98,6 +105,8 @@ __device__ __forceinline__ int march_forward(const Common& P, const RayF& r, con
     }
   }
   if (cap > 0) P.o.ccount[out] = kept;
+  if constexpr (RANGE)
+    P.o.range[out] = rfirst < 0 ? make_int2(0, 0) : make_int2(rfirst, rlast + 1);
   if constexpr (!SEG) {
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) C[ch] = fmaf(T, P.o.bg[ch], C[ch]);
@@ -292,7 +301,8 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
                                                const float Cf[3], float Df, const float gC[3],
                                                float gD, float* __restrict__ grad, int k0 = 0,
                                                int k1 = 0, float T0 = 1.f,
-                                               const float* S0 = nullptr, float SD0 = 0.f) {
+                                               const float* S0 = nullptr, float SD0 = 0.f,
+                                               int2 range = make_int2(0, 0x7fffffff)) {
   const int rm2x = P.g.rx - 2, rm2y = P.g.ry - 2, rm2z = P.g.rz - 2;
   int cx = -1, cy = -1, cz = -1;
   bool empty = true, dirty = false;
@@ -308,8 +318,10 @@ __device__ __forceinline__ void march_backward(const Common& P, const RayF& r, c
     SD = SD0;
   }
   const float dt = r.dt;
-  const int k_end = SEG ? k1 : r.n;
-  for (int k = SEG ? k0 : 0; k < k_end; ++k) {
+  // without SEG, `range` limits the march to the ray's compositing samples:
+  // nothing before range.x composites (T = 1, sums 0 there), nothing after
+  const int k_end = SEG ? k1 : (range.y < r.n ? range.y : r.n);
+  for (int k = SEG ? k0 : range.x; k < k_end; ++k) {
     const float kf = (float)k;
     int ix, iy, iz;
     float fx, fy, fz;

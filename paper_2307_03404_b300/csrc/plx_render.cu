@@ -21,7 +21,7 @@
 
 namespace plx {
 
-template <int STORE, bool COUNT, int MINB>
+template <int STORE, bool COUNT, int MINB, bool RANGE = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __restrict__ depth,
           float* __restrict__ state, int32_t* __restrict__ counts) {
@@ -43,7 +43,8 @@ k_forward(const __grid_constant__ Common P, float* __restrict__ rgb, float* __re
   sh_basis(r.dir, Y);
   float C[3], D, T;
   int n_all = 0, n_occ = 0;
-  march_forward<STORE, COUNT>(P, r, Y, C, D, T, n_all, n_occ, id.out, P.o.ccap);
+  march_forward<STORE, COUNT, false, false, RANGE>(P, r, Y, C, D, T, n_all, n_occ, id.out,
+                                                   P.o.ccap);
   rgb[3 * id.out] = C[0];
   rgb[3 * id.out + 1] = C[1];
   rgb[3 * id.out + 2] = C[2];
@@ -182,7 +183,10 @@ k_backward_grid(const __grid_constant__ Common P, const float* __restrict__ rgb_
         float Cf[3], gC[3], Df, gD;
         loss = ray_residual(P, r, id.out, dz, (float)(1.0 / (double)M), rgb_t, rgb, depth, Cf,
                             gC, Df, gD);
-        if (!loss_only) march_backward<STORE>(P, r, Y, Cf, Df, gC, gD, grad);
+        if (!loss_only) {
+          const int2 range = P.o.range ? __ldg(P.o.range + id.out) : make_int2(0, 0x7fffffff);
+          march_backward<STORE>(P, r, Y, Cf, Df, gC, gD, grad, 0, 0, 1.f, nullptr, 0.f, range);
+        }
       }
     }
   }
@@ -275,6 +279,7 @@ k_backward_grid_cached(const __grid_constant__ Common P, const float* __restrict
 // of front to back costs about 1e-8 absolute, over 1e-5 of a 1e-3 floor.)
 static bool use_seg(const Common& P) {
   return P.ct.n_tiles * 32 <= (int64_t)P.g.seg_rays && !(P.o.stop_T > 0.f) && P.o.ccap == 0 &&
+         !P.o.range &&
          P.o.color_act == PLX_ACT_SIGMOID;
 }
 
@@ -299,10 +304,14 @@ void launch_forward(int store, int minb, const Common& P, float* rgb, float* dep
     return;
   }
   const unsigned blocks = (unsigned)((P.ct.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
-#define PLX_FWD(S, M)                                                               \
-  if (counts)                                                                       \
-    k_forward<S, true, M><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts);  \
-  else                                                                              \
+#define PLX_FWD(S, M)                                                                     \
+  if (counts && P.o.range)                                                                \
+    k_forward<S, true, M, true><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts);  \
+  else if (counts)                                                                        \
+    k_forward<S, true, M><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts);        \
+  else if (P.o.range)                                                                     \
+    k_forward<S, false, M, true><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts); \
+  else                                                                                    \
     k_forward<S, false, M><<<blocks, kBlock, 0, s>>>(P, rgb, depth, state, counts)
   PLX_DISPATCH_SM3(store, minb, PLX_FWD);
 #undef PLX_FWD

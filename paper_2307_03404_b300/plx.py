@@ -76,7 +76,7 @@ class RenderOpts(C.Structure):
                 ("bg", C.c_float * 3), ("lambda_d", C.c_float), ("max_samples", C.c_int32),
                 ("color_act", C.c_int32), ("depth_is_z", C.c_int32), ("pose_flags", C.c_int32),
                 ("sample_cache", C.c_void_p), ("sample_cap", C.c_int32),
-                ("sample_rays", C.c_int64)]
+                ("sample_rays", C.c_int64), ("ray_range", C.c_void_p)]
 
 
 SYMBOLS = ["plx_last_error", "plx_version", "plx_grid_create", "plx_grid_upload",
@@ -380,6 +380,7 @@ class SampleCache:
         c.sample_cap = self.cap
         c.sample_rays = self.n_rays
         c._cache = self
+        c._range = getattr(o, "_range", None)
         return c
 
     def counts(self):
@@ -389,6 +390,35 @@ class SampleCache:
             raise ValueError("a cache with cap 0 is never filled")
         off = 5 * self.cap * self.n_rays  # float4 [cap][n] then int32 [cap][n], in 4-byte words
         return self.buf[off:off + self.n_rays].view(torch.int32)
+
+
+class RayRange:
+    """A compositing-range buffer (plx_render_opts.ray_range) for calls over
+    ``n_rays`` rays: the forward writes each ray's first and one-past-last
+    compositing sample, and the re-marching grid adjoint of the same rays
+    marches only that range (same gradients, fewer samples: the per-ray state
+    a recomputing adjoint keeps, 8 bytes per ray). ``opts(o)`` returns a copy
+    of the options naming it."""
+
+    def __init__(self, n_rays, device="cuda"):
+        self.n_rays = int(n_rays)
+        if self.n_rays < 0:
+            raise ValueError("n_rays must be >= 0")
+        self.buf = torch.zeros(max(self.n_rays, 1), 2, dtype=torch.int32, device=device)
+
+    def opts(self, o):
+        """A copy of the options ``o`` naming this range buffer (the copy
+        keeps the buffer, and any sample cache ``o`` names, alive)."""
+        c = RenderOpts.from_buffer_copy(o)
+        c.ray_range = self.buf.data_ptr()
+        c._cache = getattr(o, "_cache", None)
+        c._range = self
+        return c
+
+    def ranges(self):
+        """[n_rays, 2] int32: first and one past the last compositing sample
+        of each ray from the last forward that wrote this buffer."""
+        return self.buf[:self.n_rays]
 
 
 def opts_from_dict(d):

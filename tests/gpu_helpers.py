@@ -43,15 +43,20 @@ class GpuCase:
         self.grid.check()
         return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
 
-    def backward_grid(self, opts, rgb_t, depth_t, rays=None, cache_cap=None):
+    def backward_grid(self, opts, rgb_t, depth_t, rays=None, cache_cap=None, ray_range=False):
         """Forward then grid adjoint; with cache_cap, through a sample cache
-        of that many samples per ray (self.cache keeps it for inspection)."""
+        of that many samples per ray (self.cache keeps it for inspection);
+        with ray_range, the forward writes each ray's compositing range and
+        the re-marching adjoint marches only that (self.range keeps it)."""
         o = plx.opts_from_dict(opts)
         rr = None if rays is None else (dev(rays[0], torch.int32), dev(rays[1], torch.int32))
+        n = self.cams.n_pixels() if rays is None else len(rays[1])
         if cache_cap is not None:
-            n = self.cams.n_pixels() if rays is None else len(rays[1])
             self.cache = plx.SampleCache(n, cache_cap)
             o = self.cache.opts(o)
+        if ray_range:
+            self.range = plx.RayRange(n)
+            o = self.range.opts(o)
         out = plx.render_forward(self.grid, self.cams, o, rays=rr)
         grad, loss = plx.render_backward_grid(self.grid, self.cams, o, dev(rgb_t), dev(depth_t),
                                               out["rgb"], out["depth"], rays=rr)

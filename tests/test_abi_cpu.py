@@ -73,7 +73,7 @@ int main(void) {
   S(plx_render_opts); P(plx_render_opts, bg); P(plx_render_opts, lambda_d);
   P(plx_render_opts, max_samples); P(plx_render_opts, depth_is_z);
   P(plx_render_opts, sample_cache); P(plx_render_opts, sample_cap);
-  P(plx_render_opts, sample_rays);
+  P(plx_render_opts, sample_rays); P(plx_render_opts, ray_range);
   return 0;
 }
 """)
@@ -145,6 +145,26 @@ def test_sample_cache_binding_layout():
     assert off.opts(plx.make_opts(0.1)).sample_cache is None
     with pytest.raises(ValueError):
         off.counts()
+
+
+def test_ray_range_binding_layout():
+    """A compositing-range buffer is int32 [n][2], 8-byte aligned, and options
+    naming it keep it alive together with a sample cache named before or
+    after (host buffers: only the binding is checked here)."""
+    import torch
+
+    from paper_2307_03404_b300 import plx
+
+    rr = plx.RayRange(10, device="cpu")
+    assert rr.ranges().shape == (10, 2) and rr.ranges().dtype == torch.int32
+    assert rr.buf.data_ptr() % 8 == 0
+    c = plx.SampleCache(10, 3, device="cpu")
+    for o in (c.opts(rr.opts(plx.make_opts(0.1))), rr.opts(c.opts(plx.make_opts(0.1)))):
+        assert o.ray_range == rr.buf.data_ptr() and o.sample_cache == c.buf.data_ptr()
+        assert o._range is rr and o._cache is c
+    assert plx.make_opts(0.1).ray_range is None
+    with pytest.raises(ValueError):
+        plx.RayRange(-1, device="cpu")
 
 
 def test_grid_grow_argument_errors(lib):

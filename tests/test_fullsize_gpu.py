@@ -42,8 +42,12 @@ def keyframe():
     return sc.grid, cam, rgb_t, depth_t, opts, ref
 
 
-@pytest.mark.parametrize("cache", [None, "fit"])
+@pytest.mark.parametrize("cache", [None, "fit", "range", "range+small"])
 def test_dense_keyframe_adjoint_against_oracle(keyframe, cache):
+    """cache None: the re-marching adjoint; "fit": a sample cache that holds
+    every ray; "range": the re-march over each ray's compositing range;
+    "range+small": a cache of 8 samples per ray, most rays overflowing it
+    and re-marching over their range."""
     g, cam, rgb_t, depth_t, opts, ref = keyframe
     grid = plx.Grid.from_scene(g, "f32")
     cams = plx.CameraSet([cam])
@@ -51,6 +55,10 @@ def test_dense_keyframe_adjoint_against_oracle(keyframe, cache):
     if cache == "fit":
         sc_ = plx.SampleCache.sized_for(grid, cams, o)
         o = sc_.opts(o)
+    if cache in ("range", "range+small"):
+        o = plx.RayRange(cams.n_pixels()).opts(o)
+    if cache == "range+small":
+        o = plx.SampleCache(cams.n_pixels(), 8).opts(o)
     fw = plx.render_forward(grid, cams, o)
     grad, loss = plx.render_backward_grid(grid, cams, o, dev(rgb_t), dev(depth_t), fw["rgb"],
                                           fw["depth"])

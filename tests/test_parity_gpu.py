@@ -193,6 +193,40 @@ def test_backward_grid_sphere_scene(sphere, depth_is_z, act, bg, cache_cap):
     assert np.all(gpad == 0)
 
 
+@pytest.mark.parametrize("cache_cap", [None, 3])
+@pytest.mark.parametrize("stop_T", [0.0, 1e-2])
+def test_backward_grid_over_the_compositing_range(sphere, cache_cap, stop_T):
+    """The forward writes each ray's compositing range (first sample with
+    sigma > 0, one past the last) and the re-marching adjoint marches only
+    that: the oracle's gradients (which come from the full march), with and
+    without early stopping and with a cache so small that most rays
+    overflow it and re-march over their range. The ranges are the first
+    and last kept samples of a cached forward on the same rays."""
+    g, cam, _, opts = sphere
+    opts = dict(opts, depth_is_z=True, bg=(0.3, 0.2, 0.1), lambda_d=0.7, stop_T=stop_T)
+    rgb_t, depth_t = sphere_targets(sphere, True)
+    case = GpuCase(g, [cam])
+    gd, gs, gpad, loss = case.backward_grid(opts, rgb_t, depth_t, cache_cap=cache_cap,
+                                            ray_range=True)
+    ref = oracle.grad_grid(g, [cam], opts, rgb_t, depth_t)
+    assert loss[1] == ref.M and abs(loss[0] - ref.loss) <= 1e-5 * ref.loss
+    assert norm_err(gd, ref.grad_density) <= TOL_GRAD
+    assert norm_err(gs, ref.grad_sh) <= TOL_GRAD
+    assert np.all(gpad == 0)
+    rng = case.range.ranges().cpu().numpy()
+    n = rng.shape[0]
+    full = plx.SampleCache(n, 512)
+    plx.render_forward(case.grid, case.cams, full.opts(plx.opts_from_dict(opts)), state=False)
+    kept = full.counts().cpu().numpy()
+    ck = full.buf[4 * 512 * n: 5 * 512 * n].view(torch.int32).view(512, n).cpu().numpy()
+    assert kept.max() <= 512 and (kept == 0).any() and (kept > 0).any()
+    has = kept > 0
+    np.testing.assert_array_equal(rng[has, 0], ck[0, has])
+    np.testing.assert_array_equal(rng[has, 1], ck[kept[has] - 1, np.nonzero(has)[0]] + 1)
+    assert np.all(rng[~has] == 0)
+    assert np.all(rng[has, 1] - rng[has, 0] >= kept[has])
+
+
 @pytest.mark.parametrize("cache_cap", [None, 8])
 def test_backward_grid_sparse_list_mode_accumulates(cache_cap):
     g = scenes.tiny_grid(7, seed=31, alloc_frac=0.6, sigma_mean=2.0, sigma_std=2.0)
