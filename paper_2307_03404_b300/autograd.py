@@ -6,7 +6,9 @@ of the grid values; its gradient is the analytic adjoint of Eq. 6-10
 (``plx_render_backward_grid``). The forward renders (``plx_render_forward``)
 and takes the loss alone (the adjoint entry with no gradient buffer); the
 adjoint runs only when autograd asks for the gradient, from the forward's
-colour and depth, recomputing the per-sample transmittance. Options naming a
+colour and depth, recomputing the per-sample transmittance over each ray's
+compositing range (the forward writes it, 8 bytes per ray, unless the options
+name a ``plx.RayRange`` already; the same gradient as a full re-march). Options naming a
 sample cache (``plx.SampleCache.opts``) make that adjoint read back the
 forward's compositing samples instead of re-marching (the cache must not be
 refilled between the forward and the backward). The values are uploaded into
@@ -51,6 +53,9 @@ class MappingLoss(torch.autograd.Function):
     @staticmethod
     def forward(ctx, density, sh, grid, cams, opts, rgb_target, depth_target, rays):
         _upload_if_changed(grid, density, sh)
+        if not opts.ray_range:  # the options copy keeps the range alive for backward
+            n = cams.n_pixels() if rays is None else int(rays[1].shape[0])
+            opts = plx.RayRange(n, device=rgb_target.device).opts(opts)
         out = plx.render_forward(grid, cams, opts, rays=rays, state=False)
         _, loss = plx.render_backward_grid(grid, cams, opts, rgb_target, depth_target,
                                            out["rgb"], out["depth"], rays=rays, grad=False)
