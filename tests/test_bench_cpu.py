@@ -75,6 +75,15 @@ def test_roofline_bound_is_the_closest_ceiling(monkeypatch):
                              "m", clocks)
     assert b["bound"] == "l2_atomic" and abs(b["frac"] - 1.0) < 1e-12
     assert b["l2"]["red"]["peak"] == 40e9
+    # with the probe's measured issue rate, instruction issue is held against
+    # it instead of the nominal rate: 480 G/s against 600 G/s = 0.8
+    ceil_m = dict(ceil, issue_warp_inst_per_s=600e9)
+    rec["red_requests_per_launch"] = 0.1e9
+    b = bench.roofline_block("backward_grid", "w", "f32", 2000, 5.0, ceil_m, 1e8, 1e12, "m",
+                             clocks)
+    assert b["bound"] == "alu" and abs(b["frac"] - 0.8) < 1e-12
+    assert b["issue"]["peak"] == 600e9 and b["issue"]["nominal_peak"] == 800e9
+    assert b["issue"]["peak_basis"].startswith("measured")
     monkeypatch.setattr(bench, "measured_profile", lambda k, w, s: None)
     b = bench.roofline_block("backward_grid", "w", "f32", 2000, 5.0, ceil, 1e8, 1e12, "m",
                              clocks)
